@@ -1,0 +1,335 @@
+"""Throughput of the PIE MLFMA matrix-vector product on one GB300 (or N replicas).
+
+Workload: PEC sphere R = 1 m, icosahedral mesh subdivided 7 times
+(327,680 triangles, 491,520 RWG functions, N = 819,200 unknowns -- the
+"1M unknowns" point), kR = 1e-3, 7-level MLFMA (leaf box 1/32 m),
+tau = 7, kappa a = 0.06, N_theta = 8 (P = 128).  One step = one product
+y = Z x (all stages: coefficients, near part, aggregation, interpolation,
+translations at levels 3..7, anterpolation, disaggregation, assembly) on a
+complex-normal x (seed 1234) resident in HBM.  The headline `value` is the
+MIXED form (near part complex float, far part complex double); the plain
+FP64 form is reported beside it.
+
+--impl reference times the CPU FP64 oracle (the dense Galerkin product,
+computed row by row) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="pec_sphere_icosphere7_1M", mesh="icosphere n=7, R=1 m", triangles=327680,
+                rwg=491520, N=819200, kR=1e-3, levels=7, leaf_m=1.0 / 32, tau=7, kappa_a=0.06, ntheta=8, P=128,
+                nrhs=1)
+METRIC = "PIE MLFMA matvecs/s (1M unk)"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-rows", type=int, default=4, help="rows of the dense oracle product for the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic(pr, stage, mixed):
+    """(bound, amount, unit) of one launch group of a stage for one product."""
+    P = pr.P
+    L = pr.L
+    T = pr.T
+    c_far = 16  # far part is complex double in both forms
+    if stage == "near":
+        if mixed:
+            # FP32 moments read once (8 complex64 per pair) + source coefficients + potentials
+            return "hbm", pr.near_pairs * 64 + T * 6 * 16 * 2, "bytes"
+        return "alu", pr.near_pairs * 12 * 8, "flops"
+    if stage == "translation":
+        nl = sum(len(pr.level(l)[2]) for l in range(3, L + 1))
+        return "alu", nl * 5 * P * 8, "flops"
+    if stage in ("interpolation", "anterpolation"):
+        nc = sum(pr.boxes[l] for l in range(4, L + 1))
+        return "alu", nc * 5 * P * P * 4, "flops"
+    if stage in ("aggregation", "disaggregation"):
+        return "alu", T * P * 8 * 8, "flops"
+    return "hbm", pr.N * c_far * 2, "bytes"
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1806_04164_gb300 as pg
+    import pie_inputs as pi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    xyz, tri = pi.icosphere(7)
+    mesh = pg.Mesh(xyz, tri)
+    k0 = 1e-3
+    stream = torch.cuda.current_stream()
+    x_host = pi.complex_normal(mesh.nt + mesh.ne, 1234)
+    results = {}
+    for mode, prec in (("mixed", pg.PIE_MIXED), ("fp64", pg.PIE_FP64)):
+        t0 = time.time()
+        pr = pg.Problem(mesh, k0, 7, root_side=2.0, precision=prec)
+        setup_s = time.time() - t0
+        x = torch.from_numpy(x_host).to(pr.torch_dtype).cuda()
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            pr.apply(x, y)
+        torch.cuda.synchronize()
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pr.profile_begin(args.steps)
+        with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                pr.apply(x, y)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        stage_ms, napplies = pr.profile_end()
+        ms_max = max_over_ranks(ms)
+        # end to end through the public API with host buffers
+        xh = torch.from_numpy(x_host).to(pr.torch_dtype).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        xd = torch.empty_like(x)
+        yd = torch.empty_like(x)
+        for _ in range(2):
+            xd.copy_(xh, non_blocking=True)
+            pr.apply(xd, yd)
+            yh.copy_(yd, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            xd.copy_(xh, non_blocking=True)
+            pr.apply(xd, yd)
+            yh.copy_(yd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+        launches_per = 1 + 1 + 1 + (pr.L - 3) + (pr.L - 2) + (pr.L - 3) + 1 + 1
+        results[mode] = dict(pr=pr, ms=ms_max, stage_ms=stage_ms, napplies=napplies, clocks=clk.summary(),
+                             e2e_ms=e2e_ms, setup_s=setup_s, launches=launches_per * args.steps,
+                             bytes_io=x.numel() * x.element_size(), device_bytes=pr.device_bytes,
+                             near_pairs=pr.near_pairs)
+        del x, y, xd, yd
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    K = args.steps
+    hbm, hbm_src = peaks()
+    main = results["mixed"]
+    pr = main["pr"]
+    dom = max(main["stage_ms"], key=main["stage_ms"].get)
+    bound, amount, unit = algorithmic(pr, dom, True)
+    per_launch_ms = main["stage_ms"][dom] / max(1, main["napplies"])
+    if bound == "hbm":
+        achieved = amount / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": hbm_src, "algorithmic_bytes": amount, "traffic": None}
+    else:
+        achieved = amount / (per_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal FP64",
+                "algorithmic_flops": amount, "traffic": None}
+    stage_share = {k: round(v / sum(main["stage_ms"].values()), 4) for k, v in main["stage_ms"].items()}
+    fp = results["fp64"]
+    line = {
+        "metric": METRIC,
+        "value": world * K / (main["ms"] * 1e-3),
+        "unit": "matvecs/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": main["ms"] / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64 near + c128 far (mixed)",
+        "data": "synthetic (icosphere mesh, seeded complex-normal x)",
+        "config": dict(WORKLOAD, precision="mixed", parallelism=f"replicas{world}",
+                       l2="working set > L2 (near moments %.1f GB), no flush" % (main["near_pairs"] * 64 / 1e9)),
+        "e2e": {"value": world * K / (main["e2e_ms"] * 1e-3), "unit": "matvecs/s",
+                "h2d_bytes_per_step": main["bytes_io"], "d2h_bytes_per_step": main["bytes_io"]},
+        "gpu_launches": main["launches"],
+        "roofline": roof,
+        "stage_ms_per_step": {k: v / K for k, v in main["stage_ms"].items()},
+        "stage_share": stage_share,
+        "fp64": {"value": world * K / (fp["ms"] * 1e-3), "ms_per_step": fp["ms"] / K,
+                 "stage_ms_per_step": {k: v / K for k, v in fp["stage_ms"].items()},
+                 "e2e_value": world * K / (fp["e2e_ms"] * 1e-3), "setup_s": fp["setup_s"]},
+        "setup_s": main["setup_s"],
+        "device_bytes": main["device_bytes"],
+        "clocks": main["clocks"],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_rows)
+    print(json.dumps(line))
+
+
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, ROOTDIR)
+import numpy as np
+import pie_inputs as pi
+from oracle.dense import rows
+from oracle.mesh import build_topology
+xyz, tri = pi.icosphere(7)
+top = build_topology(xyz, tri)
+x = pi.complex_normal(top.N, 1234)
+which = [0, top.E // 2, top.E + 5, top.N - 1][:NROWS]
+rows(top, 1e-3, which[:1], x)          # warm-up (caches, page-in)
+t0 = time.time()
+rows(top, 1e-3, which, x)
+dt = time.time() - t0
+print(json.dumps({"rows": len(which), "seconds": dt, "N": top.N}))
+"""
+
+
+def cpu_baseline(nrows):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = CPU_SNIPPET.replace("ROOTDIR", repr(ROOT)).replace("NROWS", str(int(nrows)))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        return {"error": out.stderr.strip().splitlines()[-1] if out.stderr else "failed"}
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    value = d["rows"] / d["seconds"] / d["N"]
+    return {"value": value, "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{d['rows']} rows of the dense FP64 Galerkin product y = Z x on the same "
+                      f"819,200-unknown sphere ({d['seconds']:.1f} s, single thread); "
+                      f"matvecs/s = rows/s / N"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import pie_inputs as pi
+    from oracle.dense import rows
+    from oracle.mesh import build_topology
+    xyz, tri = pi.icosphere(7)
+    top = build_topology(xyz, tri)
+    x = pi.complex_normal(top.N, 1234)
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        rows(top, 1e-3, [int(rng.integers(top.N))], x)
+    t0 = time.time()
+    for _ in range(args.steps):
+        rows(top, 1e-3, [int(rng.integers(top.N))], x)
+    dt = time.time() - t0
+    value = args.steps / dt / top.N
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "matvecs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic (icosphere mesh, seeded complex-normal x)", "config": dict(WORKLOAD, precision="fp64"),
+        "cpu_baseline": {"value": value, "unit": "matvecs/s", "cores": 1, "kind": "oracle",
+                         "sample": "one row of the dense FP64 Galerkin product per step on the same sphere; "
+                                   "matvecs/s = rows/s / N"},
+        "e2e": {"value": value, "unit": "matvecs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,215 @@
+/*
+ * pie.h -- C ABI of the GB300 library for the MLFMA matrix-vector product of
+ * the potential integral equations (PIEs) of Guer & Erguel (2017).
+ *
+ * The operator is the Galerkin matrix Z of Eqs. (1)-(2) (Section 2): J on RWG
+ * functions (one per interior edge) and sigma = n'.A on pulse functions (one
+ * per triangle), N = E + T.  With <a,g,b> = int int a(r).b(r') g dr' dr and
+ * g = exp(i k0 R)/(4 pi R):
+ *
+ *     Z_JJ[m,n] = mu0 <f_m, g, f_n>        Z_Js[m,t] = <div f_m, g, p_t>
+ *     Z_sJ[t,n] = <p_t, g, div' f_n>       Z_ss[t,u] = w^2 eps0 <p_t, g, p_u>
+ *
+ * (Eq. (1) tested tangentially with the RWG functions, Eq. (2) with the
+ * pulses, the gradient of g moved onto the testing function by parts as
+ * Section 3 describes).  Constants: mu0 = 4 pi 1e-7, c0 = 299792458,
+ * eps0 = 1/(mu0 c0^2), w = k0 c0.  Unknowns and results are ordered
+ * [E RWG coefficients ; T pulse coefficients]; edges are numbered in
+ * increasing (min vertex, max vertex) order; the "+" triangle of an edge is
+ * the one whose counter-clockwise vertex order runs along the edge from its
+ * smaller to its larger vertex.
+ *
+ * The product splits (Section 3) into a near part -- exact pair integrals
+ * between triangles in neighbouring leaf boxes of a cubic oct-tree
+ * (one-box buffer) -- and a far part computed by aggregation, interpolation,
+ * diagonal translation with the approximate stable diagonalization of
+ * Eqs. (4)-(5), anterpolation and disaggregation.
+ *
+ * Conventions for every call:
+ *  - Return value: PIE_OK or an error code; pie_last_error() gives a message
+ *    (thread-local, valid until the next call on the same thread).  No call
+ *    throws or aborts.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it asynchronously unless stated.
+ *  - Complex arrays are interleaved (re, im) pairs: PIE_C128 = two doubles,
+ *    PIE_C64 = two floats.
+ *  - The library owns all memory it allocates; objects are not thread-safe.
+ */
+#ifndef PIE_H
+#define PIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PIE_OK = 0,
+  PIE_ERR_PARAM = 1,        /* invalid argument */
+  PIE_ERR_NONMANIFOLD = 2,  /* an edge is shared by more than two triangles */
+  PIE_ERR_DEGENERATE = 3,   /* a triangle has zero area or repeated vertices */
+  PIE_ERR_ORIENTATION = 4,  /* two triangles traverse a shared edge the same way */
+  PIE_ERR_OOM = 5,          /* device or host allocation failed */
+  PIE_ERR_CUDA = 6,         /* a CUDA runtime call failed */
+  PIE_ERR_LEAF = 7,         /* leaf box smaller than 1.5 x the longest edge */
+  PIE_ERR_NOCONV = 8,       /* GMRES did not reach the tolerance */
+  PIE_ERR_BREAKDOWN = 9,    /* GMRES Arnoldi breakdown */
+  PIE_ERR_NAN = 10          /* NaN or Inf met in the iteration */
+} pie_status;
+
+typedef enum { PIE_C128 = 0, PIE_C64 = 1 } pie_dtype;
+
+/* Arithmetic of the product:
+ *  PIE_FP64  everything in complex double (inputs/outputs PIE_C128);
+ *  PIE_FP32  near and far parts in complex float (inputs/outputs PIE_C64);
+ *  PIE_MIXED near part in complex float (pair moments stored as float),
+ *            far part in complex double (inputs/outputs PIE_C128).
+ * Setup (pair integrals, translation operators, filters) is always FP64. */
+typedef enum { PIE_FP64 = 0, PIE_FP32 = 1, PIE_MIXED = 2 } pie_precision;
+
+typedef struct pie_mesh pie_mesh;
+typedef struct pie_problem pie_problem;
+
+typedef struct {
+  int levels;        /* L >= 3; level 1 is the root box, translations at 3..L */
+  double root_side;  /* side of the root cube in metres; <= 0: largest
+                        bounding-box extent.  The cube is centred on the
+                        vertex bounding-box centre. */
+  int tau;           /* truncation number of Eq. (5) */
+  double kappa_a;    /* x = (k0 / s_l) a_l, the same at every level, so the
+                        scale factor of Eq. (4) is s_l = k0 a_l / x */
+  int ntheta;        /* angular samples: ntheta Gauss-Legendre nodes in
+                        cos(theta) x 2 ntheta azimuths, P = 2 ntheta^2 */
+  int precision;     /* pie_precision */
+} pie_params;
+
+typedef struct {
+  int64_t N, E, T;            /* unknowns, RWG functions, triangles */
+  int32_t L, P;               /* levels, angular samples per box */
+  int64_t boxes[24];          /* occupied boxes per level, index = level */
+  int64_t near_pairs;         /* triangle pairs in the near part */
+  int64_t device_bytes;       /* device memory held by the problem */
+  double leaf_size;           /* leaf box side in metres */
+} pie_info;
+
+typedef struct {
+  int32_t iterations;         /* Arnoldi steps taken */
+  double rel_residual;        /* ||b - Z x|| / ||b||, recomputed in FP64 */
+  double seconds;             /* wall time of the solve */
+} pie_solve_stats;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* pie_last_error(void);
+
+/* Default parameters: levels 3, root_side 0, tau 7, kappa_a 0.06, ntheta 8,
+ * precision PIE_FP64 (the values of the error search of Eqs. (4)-(5)). */
+void pie_params_default(pie_params* p);
+
+/* Surface mesh (Section 2: triangulated surface S).  xyz: nv x 3 doubles
+ * (metres, host); tri: nt x 3 vertex indices (host, counter-clockwise seen
+ * from the side the normal points to).  The library copies both arrays and
+ * builds the RWG table.  Boundary edges (one triangle) carry no RWG, so open
+ * surfaces are allowed.  Errors: PIE_ERR_PARAM (index out of range, nt = 0),
+ * PIE_ERR_DEGENERATE, PIE_ERR_NONMANIFOLD, PIE_ERR_ORIENTATION. */
+pie_status pie_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                           pie_mesh** out);
+void pie_mesh_destroy(pie_mesh* m);
+/* Counts of the mesh (host values). */
+pie_status pie_mesh_info(const pie_mesh* m, int64_t* nv, int64_t* nt, int64_t* ne);
+/* Edge table (host arrays, E x 2 each): vertex pairs (min, max), triangles
+ * (T+, T-), free vertices opposite the edge in (T+, T-).  Any pointer may be
+ * NULL. */
+pie_status pie_mesh_edges(const pie_mesh* m, int32_t* edges, int32_t* edge_tri, int32_t* edge_free);
+
+/* Operator set-up for wavenumber k0 (rad/m): oct-tree and lists (host),
+ * near pair integrals, radiation tables, translation operators of Eq. (5)
+ * and interpolation filters (device kernels, FP64).  Synchronises the
+ * stream before returning.  Errors: PIE_ERR_PARAM, PIE_ERR_LEAF, PIE_ERR_OOM,
+ * PIE_ERR_CUDA. */
+pie_status pie_problem_create(const pie_mesh* m, double k0, const pie_params* p, void* stream,
+                              pie_problem** out);
+void pie_problem_destroy(pie_problem* pr);
+pie_status pie_problem_info(const pie_problem* pr, pie_info* info);
+
+/* Tree export for bit-exact checks (host arrays).
+ * pie_problem_perm: perm[T], the mesh triangle at each tree position
+ *   (triangles sorted by (leaf Morton key, triangle index)).
+ * pie_problem_level: for level l in [1, L]: keys[nb] (Morton keys, sorted);
+ *   for l >= 3 also the interaction lists in CSR form: ptr[nb+1], idx[ptr[nb]]
+ *   (source box numbers, ascending) and off[ptr[nb]] (offset code 0..315 of
+ *   destination minus source box index, lexicographic over {-3..3}^3 without
+ *   {-1..1}^3).  Call with NULL arrays to get nb and the list length.
+ * pie_problem_near: leaf near lists, ptr[nleaf+1] and idx[...].  */
+pie_status pie_problem_perm(const pie_problem* pr, int64_t* perm);
+pie_status pie_problem_level(const pie_problem* pr, int level, int64_t* nb, int64_t* nlist,
+                             int64_t* keys, int64_t* ptr, int64_t* idx, int32_t* off);
+pie_status pie_problem_near(const pie_problem* pr, int64_t* nlist, int64_t* ptr, int64_t* idx);
+
+/* y = Z x (Section 3: one MVM).  x, y: device buffers of N x nrhs complex
+ * numbers, column-major (column j at offset j*N), caller-owned, not
+ * overlapping.  dtype must be PIE_C128 for PIE_FP64 / PIE_MIXED problems and
+ * PIE_C64 for PIE_FP32.  Asynchronous on the stream.  Errors: PIE_ERR_PARAM,
+ * PIE_ERR_CUDA. */
+pie_status pie_apply(pie_problem* pr, const void* x, void* y, int nrhs, int dtype, void* stream);
+
+/* y = Z_near x: the near part of the product alone (Section 3: interactions
+ * of triangles in neighbouring leaf boxes, one-box buffer, computed exactly
+ * as in the dense matrix).  Same arguments and errors as pie_apply.  Useful
+ * as a sparse preconditioner and for checking the near part by itself. */
+pie_status pie_apply_near(pie_problem* pr, const void* x, void* y, int nrhs, int dtype, void* stream);
+
+/* Per-stage timing of products (CUDA events recorded on the apply stream
+ * around each stage).  pie_profile_begin arms recording for the next
+ * max_applies single-column products; pie_profile_end waits for them and
+ * writes the summed milliseconds of the PIE_NSTAGES stages to stage_ms
+ * (host, may be NULL) and the number of recorded products to applies.
+ * Stages, in order: 0 local coefficients, 1 near part, 2 leaf aggregation,
+ * 3 interpolation (all levels), 4 translation (all levels), 5 anterpolation,
+ * 6 leaf disaggregation, 7 Galerkin assembly. */
+#define PIE_NSTAGES 8
+pie_status pie_profile_begin(pie_problem* pr, int max_applies);
+pie_status pie_profile_end(pie_problem* pr, double* stage_ms, int32_t* applies);
+
+/* Stage output of the last pie_apply (first right-hand side), copied to the
+ * host after synchronising the stream: which = 0 radiated patterns S_l
+ * (after aggregation / interpolation), which = 1 incoming patterns G_l (after
+ * translation and anterpolation), 2 = per-triangle local coefficients
+ * [T][6] (a, beta_x, beta_y, beta_z, sigma, d) in tree order (level ignored),
+ * 3 = per-triangle potentials [T][6] (U, V_x, V_y, V_z, T1, T2), 4 = near
+ * pair moments [8][nnz] (m0, mt_xyz, ms_xyz, mts; entries ordered by test
+ * triangle in tree order, then by near box, then by source triangle),
+ * 5 = leaf radiation table Pi [T][P], 6 = leaf radiation table M [T][3][P]
+ * (tree order).  Patterns
+ * are [nb][5][P] complex double (converted from float in PIE_FP32). */
+pie_status pie_problem_stage(pie_problem* pr, int which, int level, double* out, void* stream);
+
+/* Right-hand side for a plane wave E = pol E0 exp(i k0 khat.r) (pol . khat =
+ * 0) with the Lorenz-gauge potentials Phi = -E0 (pol.r) exp(i k0 khat.r),
+ * A = -(E0/c0)(pol.r) khat exp(i k0 khat.r):  b_J = -<f_m, A>,
+ * b_sigma = -i w eps0 <p_t, Phi> (Eqs. (1)-(2) right-hand sides).  b: device,
+ * N complex of the problem's dtype. */
+pie_status pie_rhs_planewave(pie_problem* pr, const double khat[3], const double pol[3], double E0,
+                             void* b, int dtype, void* stream);
+
+/* Far-zone field from J (Section 2): E[d] = i w mu0/(4 pi) (I - rr) .
+ * int J exp(-i k0 r.r') dr' (factor exp(i k0 r)/r removed).  rhat: host
+ * ndir x 3; E: device ndir x 3 complex double.  x: device solution
+ * (problem dtype). */
+pie_status pie_farfield(pie_problem* pr, const void* x, const double* rhat, int64_t ndir, void* E,
+                        void* stream);
+
+/* GMRES (Section 4) on Z x = b, zero initial guess, restarted every
+ * `restart` steps, stopping when the FP64 residual ||b - Z x||/||b|| <= tol
+ * (the operator is scaled symmetrically by the inverse square roots of the
+ * diagonal magnitudes of its near part; the stopping test is on the
+ * unscaled system).  b, x: device, N complex of the problem's dtype.
+ * Synchronises the stream.  Errors: PIE_ERR_NOCONV, PIE_ERR_BREAKDOWN,
+ * PIE_ERR_NAN, PIE_ERR_CUDA. */
+pie_status pie_solve(pie_problem* pr, const void* b, void* x, double tol, int maxit, int restart,
+                     pie_solve_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIE_H */

@@ -1,0 +1,269 @@
+"""Python binding of libpie (include/pie.h): argument marshalling only.
+
+Every step of the operator runs in the CUDA library; this module converts
+numpy / torch arguments into the C ABI's plain pointers and sizes.  Device
+buffers are torch tensors on a CUDA device (complex128 for PIE_FP64 and
+PIE_MIXED problems, complex64 for PIE_FP32); streams default to torch's
+current stream.  Importing works without a GPU; creating a problem needs one
+and raises if the library has not been built.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libpie.so")
+
+PIE_FP64, PIE_FP32, PIE_MIXED = 0, 1, 2
+PIE_C128, PIE_C64 = 0, 1
+STATUS = {0: "PIE_OK", 1: "PIE_ERR_PARAM", 2: "PIE_ERR_NONMANIFOLD", 3: "PIE_ERR_DEGENERATE",
+          4: "PIE_ERR_ORIENTATION", 5: "PIE_ERR_OOM", 6: "PIE_ERR_CUDA", 7: "PIE_ERR_LEAF",
+          8: "PIE_ERR_NOCONV", 9: "PIE_ERR_BREAKDOWN", 10: "PIE_ERR_NAN"}
+
+# Parameters found by the Eq. (4)-(5) error search (truncation tau, kappa*a, N_theta).
+DEFAULT_TAU, DEFAULT_KAPPA_A, DEFAULT_NTHETA = 7, 0.06, 8
+
+
+class PieError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("root_side", ctypes.c_double), ("tau", ctypes.c_int),
+                ("kappa_a", ctypes.c_double), ("ntheta", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("E", ctypes.c_int64), ("T", ctypes.c_int64), ("L", ctypes.c_int32),
+                ("P", ctypes.c_int32), ("boxes", ctypes.c_int64 * 24), ("near_pairs", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("leaf_size", ctypes.c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+_lib = None
+EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_destroy", "pie_mesh_info",
+           "pie_mesh_edges", "pie_problem_create", "pie_problem_destroy", "pie_problem_info", "pie_problem_perm",
+           "pie_problem_level", "pie_problem_near", "pie_apply", "pie_apply_near", "pie_problem_stage", "pie_rhs_planewave",
+           "pie_farfield", "pie_solve", "pie_profile_begin", "pie_profile_end"]
+STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
+          "assembly"]
+
+
+def lib():
+    """Load libpie.so (built by build.py); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"libpie.so not built ({LIBPATH}); run paper_1806_04164_gb300/build.py")
+        L = ctypes.CDLL(LIBPATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        P64 = ctypes.POINTER(ctypes.c_int64)
+        P32 = ctypes.POINTER(ctypes.c_int32)
+        PD = ctypes.POINTER(ctypes.c_double)
+        L.pie_last_error.restype = ctypes.c_char_p
+        L.pie_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.pie_mesh_create.argtypes = [PD, i64, P32, i64, ctypes.POINTER(vp)]
+        L.pie_mesh_destroy.argtypes = [vp]
+        L.pie_mesh_info.argtypes = [vp, P64, P64, P64]
+        L.pie_mesh_edges.argtypes = [vp, P32, P32, P32]
+        L.pie_problem_create.argtypes = [vp, dbl, ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+        L.pie_problem_destroy.argtypes = [vp]
+        L.pie_problem_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.pie_problem_perm.argtypes = [vp, P64]
+        L.pie_problem_level.argtypes = [vp, i32, P64, P64, P64, P64, P64, P32]
+        L.pie_problem_near.argtypes = [vp, P64, P64, P64]
+        L.pie_apply.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.pie_apply_near.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.pie_problem_stage.argtypes = [vp, i32, i32, PD, vp]
+        L.pie_rhs_planewave.argtypes = [vp, PD, PD, dbl, vp, i32, vp]
+        L.pie_farfield.argtypes = [vp, vp, PD, i64, vp, vp]
+        L.pie_profile_begin.argtypes = [vp, i32]
+        L.pie_profile_end.argtypes = [vp, PD, P32]
+        L.pie_solve.argtypes = [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise PieError(code, lib().pie_last_error().decode())
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Mesh:
+    """Triangulated surface (pie_mesh_create)."""
+
+    def __init__(self, xyz, tri):
+        self.xyz = np.ascontiguousarray(xyz, np.float64)
+        self.tri = np.ascontiguousarray(tri, np.int32)
+        h = ctypes.c_void_p()
+        _check(lib().pie_mesh_create(_ptr(self.xyz, ctypes.c_double), self.xyz.shape[0],
+                                     _ptr(self.tri, ctypes.c_int32), self.tri.shape[0], ctypes.byref(h)))
+        self.handle = h
+        nv, nt, ne = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pie_mesh_info(h, ctypes.byref(nv), ctypes.byref(nt), ctypes.byref(ne)))
+        self.nv, self.nt, self.ne = nv.value, nt.value, ne.value
+
+    def edges(self):
+        e = np.zeros((self.ne, 2), np.int32)
+        et = np.zeros((self.ne, 2), np.int32)
+        ef = np.zeros((self.ne, 2), np.int32)
+        _check(lib().pie_mesh_edges(self.handle, _ptr(e, ctypes.c_int32), _ptr(et, ctypes.c_int32),
+                                    _ptr(ef, ctypes.c_int32)))
+        return e, et, ef
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.pie_mesh_destroy(self.handle)
+            self.handle = None
+
+
+class Problem:
+    """PIE operator for one mesh and wavenumber (pie_problem_create)."""
+
+    def __init__(self, mesh, k0, levels, root_side=0.0, tau=DEFAULT_TAU, kappa_a=DEFAULT_KAPPA_A,
+                 ntheta=DEFAULT_NTHETA, precision=PIE_FP64, stream=None):
+        self.mesh = mesh
+        self.k0 = float(k0)
+        self.precision = precision
+        p = Params(levels, root_side, tau, kappa_a, ntheta, precision)
+        h = ctypes.c_void_p()
+        _check(lib().pie_problem_create(mesh.handle, self.k0, ctypes.byref(p), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+        info = Info()
+        _check(lib().pie_problem_info(h, ctypes.byref(info)))
+        self.N, self.E, self.T, self.L, self.P = info.N, info.E, info.T, info.L, info.P
+        self.boxes = [info.boxes[l] for l in range(self.L + 1)]
+        self.near_pairs = info.near_pairs
+        self.device_bytes = info.device_bytes
+        self.leaf_size = info.leaf_size
+        self.dtype_code = PIE_C64 if precision == PIE_FP32 else PIE_C128
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.complex64 if self.dtype_code == PIE_C64 else torch.complex128
+
+    def perm(self):
+        out = np.zeros(self.T, np.int64)
+        _check(lib().pie_problem_perm(self.handle, _ptr(out, ctypes.c_int64)))
+        return out
+
+    def level(self, l):
+        nb, nl = ctypes.c_int64(), ctypes.c_int64()
+        null64 = ctypes.POINTER(ctypes.c_int64)()
+        _check(lib().pie_problem_level(self.handle, l, ctypes.byref(nb), ctypes.byref(nl), null64, null64,
+                                       null64, ctypes.POINTER(ctypes.c_int32)()))
+        keys = np.zeros(nb.value, np.int64)
+        ptr = np.zeros(nb.value + 1, np.int64)
+        idx = np.zeros(nl.value, np.int64)
+        off = np.zeros(nl.value, np.int32)
+        _check(lib().pie_problem_level(self.handle, l, ctypes.byref(nb), ctypes.byref(nl),
+                                       _ptr(keys, ctypes.c_int64), _ptr(ptr, ctypes.c_int64),
+                                       _ptr(idx, ctypes.c_int64), _ptr(off, ctypes.c_int32)))
+        return keys, ptr, idx, off
+
+    def near(self):
+        nl = ctypes.c_int64()
+        null64 = ctypes.POINTER(ctypes.c_int64)()
+        _check(lib().pie_problem_near(self.handle, ctypes.byref(nl), null64, null64))
+        ptr = np.zeros(self.boxes[self.L] + 1, np.int64)
+        idx = np.zeros(nl.value, np.int64)
+        _check(lib().pie_problem_near(self.handle, ctypes.byref(nl), _ptr(ptr, ctypes.c_int64),
+                                      _ptr(idx, ctypes.c_int64)))
+        return ptr, idx
+
+    def apply(self, x, y=None, stream=None, near_only=False):
+        """y = Z x for device tensors of shape [N] or [nrhs, N] (row j = right-hand
+        side j); near_only=True applies the near part Z_near alone."""
+        import torch
+        assert x.is_cuda and x.dtype == self.torch_dtype and x.is_contiguous()
+        if y is None:
+            y = torch.empty_like(x)
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        assert x.shape[-1] == self.N and y.shape == x.shape and y.is_contiguous()
+        fn = lib().pie_apply_near if near_only else lib().pie_apply
+        _check(fn(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), nrhs,
+                  self.dtype_code, _stream(stream)))
+        return y
+
+    def profile_begin(self, max_applies):
+        _check(lib().pie_profile_begin(self.handle, max_applies))
+
+    def profile_end(self):
+        """Summed milliseconds per stage of the products recorded since profile_begin."""
+        ms = np.zeros(len(STAGES), np.float64)
+        n = ctypes.c_int32()
+        _check(lib().pie_profile_end(self.handle, _ptr(ms, ctypes.c_double), ctypes.byref(n)))
+        return dict(zip(STAGES, ms.tolist())), n.value
+
+    def stage(self, which, level=0, stream=None):
+        if which in (0, 1):
+            n = self.boxes[level] * 5 * self.P
+            shape = (self.boxes[level], 5, self.P)
+        elif which == 4:
+            n = 8 * self.near_pairs
+            shape = (8, self.near_pairs)
+        elif which == 5:
+            n = self.T * self.P
+            shape = (self.T, self.P)
+        elif which == 6:
+            n = self.T * 3 * self.P
+            shape = (self.T, 3, self.P)
+        else:
+            n = self.T * 6
+            shape = (self.T, 6)
+        out = np.zeros(2 * n, np.float64)
+        _check(lib().pie_problem_stage(self.handle, which, level, _ptr(out, ctypes.c_double), _stream(stream)))
+        return (out[0::2] + 1j * out[1::2]).reshape(shape)
+
+    def rhs_planewave(self, khat, pol, E0=1.0, stream=None):
+        import torch
+        b = torch.empty(self.N, dtype=self.torch_dtype, device="cuda")
+        kh = np.ascontiguousarray(khat, np.float64)
+        po = np.ascontiguousarray(pol, np.float64)
+        _check(lib().pie_rhs_planewave(self.handle, _ptr(kh, ctypes.c_double), _ptr(po, ctypes.c_double), E0,
+                                       ctypes.c_void_p(b.data_ptr()), self.dtype_code, _stream(stream)))
+        return b
+
+    def farfield(self, x, rhat, stream=None):
+        import torch
+        rh = np.ascontiguousarray(rhat, np.float64)
+        E = torch.empty((rh.shape[0], 3), dtype=torch.complex128, device="cuda")
+        _check(lib().pie_farfield(self.handle, ctypes.c_void_p(x.data_ptr()), _ptr(rh, ctypes.c_double),
+                                  rh.shape[0], ctypes.c_void_p(E.data_ptr()), _stream(stream)))
+        return E
+
+    def solve(self, b, tol=1e-6, maxit=1000, restart=100, stream=None):
+        import torch
+        x = torch.zeros_like(b)
+        st = SolveStats()
+        code = lib().pie_solve(self.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), tol,
+                               maxit, restart, ctypes.byref(st), _stream(stream))
+        if code not in (0, 8):
+            _check(code)
+        return x, dict(iterations=st.iterations, rel_residual=st.rel_residual, seconds=st.seconds,
+                       converged=code == 0)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.pie_problem_destroy(self.handle)
+            self.handle = None

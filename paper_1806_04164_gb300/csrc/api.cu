@@ -1,0 +1,362 @@
+// extern "C" entry points of include/pie.h.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "problem.h"
+
+struct pie_mesh {
+  pie::Mesh m;
+};
+struct pie_problem {
+  pie::Problem p;
+};
+
+namespace pie {
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace pie
+
+using namespace pie;
+
+extern "C" {
+
+const char* pie_last_error(void) { return g_err.c_str(); }
+
+void pie_params_default(pie_params* p) {
+  if (!p) return;
+  p->levels = 3;
+  p->root_side = 0.0;
+  p->tau = 7;
+  p->kappa_a = 0.06;
+  p->ntheta = 8;
+  p->precision = PIE_FP64;
+}
+
+pie_status pie_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, pie_mesh** out) {
+  if (!out) {
+    set_error("pie_mesh_create: out is NULL");
+    return PIE_ERR_PARAM;
+  }
+  *out = nullptr;
+  pie_mesh* m = new (std::nothrow) pie_mesh;
+  if (!m) return PIE_ERR_OOM;
+  pie_status s = build_mesh(xyz, nv, tri, nt, m->m);
+  if (s != PIE_OK) {
+    delete m;
+    return s;
+  }
+  *out = m;
+  return PIE_OK;
+}
+
+void pie_mesh_destroy(pie_mesh* m) { delete m; }
+
+pie_status pie_mesh_info(const pie_mesh* m, int64_t* nv, int64_t* nt, int64_t* ne) {
+  if (!m) {
+    set_error("NULL mesh");
+    return PIE_ERR_PARAM;
+  }
+  if (nv) *nv = m->m.nv;
+  if (nt) *nt = m->m.nt;
+  if (ne) *ne = m->m.ne;
+  return PIE_OK;
+}
+
+pie_status pie_mesh_edges(const pie_mesh* m, int32_t* edges, int32_t* edge_tri, int32_t* edge_free) {
+  if (!m) {
+    set_error("NULL mesh");
+    return PIE_ERR_PARAM;
+  }
+  size_t n = m->m.edges.size();
+  if (edges) std::memcpy(edges, m->m.edges.data(), n * sizeof(int32_t));
+  if (edge_tri) std::memcpy(edge_tri, m->m.edge_tri.data(), n * sizeof(int32_t));
+  if (edge_free) std::memcpy(edge_free, m->m.edge_free.data(), n * sizeof(int32_t));
+  return PIE_OK;
+}
+
+static void free_profile(Problem& pr) {
+  for (cudaEvent_t e : pr.prof_ev) cudaEventDestroy(e);
+  pr.prof_ev.clear();
+  pr.prof_cap = pr.prof_n = 0;
+}
+
+static void free_problem(Problem& pr) {
+  free_profile(pr);
+  for (void* p : pr.allocs) cudaFree(p);
+  pr.allocs.clear();
+}
+
+pie_status pie_problem_create(const pie_mesh* m, double k0, const pie_params* par, void* stream, pie_problem** out) {
+  if (!m || !par || !out) {
+    set_error("pie_problem_create: NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  *out = nullptr;
+  if (!(k0 > 0) || par->levels < 3 || par->levels > 21 || par->tau < 0 || par->tau > 30 || par->ntheta < 1 ||
+      2 * par->ntheta * par->ntheta > 1024 || !(par->kappa_a > 0) || par->precision < 0 || par->precision > 2) {
+    set_error("pie_problem_create: parameter out of range");
+    return PIE_ERR_PARAM;
+  }
+  if (m->m.ne == 0) {
+    set_error("pie_problem_create: mesh has no interior edge");
+    return PIE_ERR_PARAM;
+  }
+  pie_problem* h = new (std::nothrow) pie_problem;
+  if (!h) return PIE_ERR_OOM;
+  Problem& pr = h->p;
+  pr.mesh = m->m;
+  pr.k0 = k0;
+  pr.w = k0 * kC0;
+  pr.par = *par;
+  pr.P = 2 * par->ntheta * par->ntheta;
+  pr.T = m->m.nt;
+  pr.E = m->m.ne;
+  pr.N = pr.T + pr.E;
+  pie_status s = build_tree(pr.mesh, par->levels, par->root_side, pr.tree);
+  if (s == PIE_OK) {
+    double aL = pr.tree.box_size(par->levels);
+    double h2max = 0;
+    for (double v : pr.mesh.h2) h2max = std::max(h2max, v);
+    if (aL * aL < 2.25 * h2max) {
+      set_error("leaf box smaller than 1.5 x the longest triangle edge");
+      s = PIE_ERR_LEAF;
+    }
+    // the power series used for s^t j_t(k w) is accurate for k w <= 4
+    if (s == PIE_OK && k0 * 3.0 * std::sqrt(3.0) * pr.tree.box_size(3) > 4.0) {
+      set_error("k0 too large for the low-frequency translation build (k0 |w| > 4 at level 3)");
+      s = PIE_ERR_PARAM;
+    }
+  }
+  if (s == PIE_OK) s = setup_device(pr, static_cast<cudaStream_t>(stream));
+  if (s != PIE_OK) {
+    free_problem(pr);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return PIE_OK;
+}
+
+void pie_problem_destroy(pie_problem* h) {
+  if (!h) return;
+  free_problem(h->p);
+  delete h;
+}
+
+pie_status pie_problem_info(const pie_problem* h, pie_info* info) {
+  if (!h || !info) {
+    set_error("NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  const Problem& pr = h->p;
+  std::memset(info, 0, sizeof(*info));
+  info->N = pr.N;
+  info->E = pr.E;
+  info->T = pr.T;
+  info->L = pr.tree.L;
+  info->P = pr.P;
+  for (int l = 1; l <= pr.tree.L && l < 24; ++l) info->boxes[l] = int64_t(pr.tree.keys[l].size());
+  info->near_pairs = pr.nnz;
+  info->device_bytes = int64_t(pr.bytes);
+  info->leaf_size = pr.tree.box_size(pr.tree.L);
+  return PIE_OK;
+}
+
+pie_status pie_problem_perm(const pie_problem* h, int64_t* perm) {
+  if (!h || !perm) {
+    set_error("NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  std::memcpy(perm, h->p.tree.perm.data(), sizeof(int64_t) * h->p.T);
+  return PIE_OK;
+}
+
+pie_status pie_problem_level(const pie_problem* h, int level, int64_t* nb, int64_t* nlist, int64_t* keys,
+                             int64_t* ptr, int64_t* idx, int32_t* off) {
+  if (!h) {
+    set_error("NULL problem");
+    return PIE_ERR_PARAM;
+  }
+  const Tree& tr = h->p.tree;
+  if (level < 1 || level > tr.L) {
+    set_error("level out of range");
+    return PIE_ERR_PARAM;
+  }
+  int64_t n = int64_t(tr.keys[level].size());
+  int64_t nl = level >= 3 ? int64_t(tr.il_idx[level].size()) : 0;
+  if (nb) *nb = n;
+  if (nlist) *nlist = nl;
+  if (keys) std::memcpy(keys, tr.keys[level].data(), sizeof(int64_t) * n);
+  if (level >= 3) {
+    if (ptr) std::memcpy(ptr, tr.il_ptr[level].data(), sizeof(int64_t) * (n + 1));
+    if (idx) std::memcpy(idx, tr.il_idx[level].data(), sizeof(int64_t) * nl);
+    if (off) std::memcpy(off, tr.il_off[level].data(), sizeof(int32_t) * nl);
+  }
+  return PIE_OK;
+}
+
+pie_status pie_problem_near(const pie_problem* h, int64_t* nlist, int64_t* ptr, int64_t* idx) {
+  if (!h) {
+    set_error("NULL problem");
+    return PIE_ERR_PARAM;
+  }
+  const Tree& tr = h->p.tree;
+  if (nlist) *nlist = int64_t(tr.near_idx.size());
+  if (ptr) std::memcpy(ptr, tr.near_ptr.data(), sizeof(int64_t) * tr.near_ptr.size());
+  if (idx) std::memcpy(idx, tr.near_idx.data(), sizeof(int64_t) * tr.near_idx.size());
+  return PIE_OK;
+}
+
+static pie_status apply_cols(pie_problem* h, const void* x, void* y, int nrhs, int dtype, void* stream, bool near) {
+  if (!h || (!x && nrhs > 0) || (!y && nrhs > 0) || nrhs < 0) {
+    set_error("pie_apply: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  Problem& pr = h->p;
+  int want = pr.io_f32() ? PIE_C64 : PIE_C128;
+  if (dtype != want) {
+    set_error("pie_apply: dtype does not match the problem precision");
+    return PIE_ERR_PARAM;
+  }
+  size_t es = pr.io_f32() ? sizeof(cf) : sizeof(cd);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int j = 0; j < nrhs; ++j) {
+    const char* xj = static_cast<const char*>(x) + es * size_t(pr.N) * j;
+    char* yj = static_cast<char*>(y) + es * size_t(pr.N) * j;
+    pie_status s = near ? apply_near_one(pr, xj, yj, st) : apply_one(pr, xj, yj, st);
+    if (s != PIE_OK) return s;
+  }
+  return PIE_OK;
+}
+
+pie_status pie_apply(pie_problem* h, const void* x, void* y, int nrhs, int dtype, void* stream) {
+  return apply_cols(h, x, y, nrhs, dtype, stream, false);
+}
+
+pie_status pie_apply_near(pie_problem* h, const void* x, void* y, int nrhs, int dtype, void* stream) {
+  return apply_cols(h, x, y, nrhs, dtype, stream, true);
+}
+
+pie_status pie_profile_begin(pie_problem* h, int max_applies) {
+  if (!h || max_applies < 1) {
+    set_error("pie_profile_begin: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  Problem& pr = h->p;
+  free_profile(pr);
+  pr.prof_ev.resize(size_t(max_applies) * kStages * 2);
+  for (auto& e : pr.prof_ev) {
+    pie_status s = cuda_check(cudaEventCreate(&e), "event create");
+    if (s != PIE_OK) {
+      e = nullptr;
+      free_profile(pr);
+      return s;
+    }
+  }
+  pr.prof_cap = max_applies;
+  pr.prof_n = 0;
+  return PIE_OK;
+}
+
+pie_status pie_profile_end(pie_problem* h, double* stage_ms, int32_t* applies) {
+  if (!h) {
+    set_error("NULL problem");
+    return PIE_ERR_PARAM;
+  }
+  Problem& pr = h->p;
+  double acc[kStages] = {0};
+  pie_status s = PIE_OK;
+  for (int a = 0; a < pr.prof_n && s == PIE_OK; ++a)
+    for (int k = 0; k < kStages && s == PIE_OK; ++k) {
+      cudaEvent_t e0 = pr.prof_ev[(size_t(a) * kStages + k) * 2], e1 = pr.prof_ev[(size_t(a) * kStages + k) * 2 + 1];
+      s = cuda_check(cudaEventSynchronize(e1), "profile sync");
+      float ms = 0;
+      if (s == PIE_OK) s = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "profile elapsed");
+      acc[k] += ms;
+    }
+  if (stage_ms)
+    for (int k = 0; k < kStages; ++k) stage_ms[k] = acc[k];
+  if (applies) *applies = pr.prof_n;
+  free_profile(pr);
+  return s;
+}
+
+pie_status pie_problem_stage(pie_problem* h, int which, int level, double* out, void* stream) {
+  if (!h || !out) {
+    set_error("NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  Problem& pr = h->p;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pie_status s = cuda_check(cudaStreamSynchronize(st), "stage sync");
+  if (s != PIE_OK) return s;
+  const void* src = nullptr;
+  size_t n = 0;
+  bool f32 = false;
+  if (which == 0 || which == 1) {
+    if (level < 3 || level > pr.tree.L) {
+      set_error("level out of range");
+      return PIE_ERR_PARAM;
+    }
+    src = which == 0 ? pr.lev[level].S : pr.lev[level].G;
+    n = size_t(pr.lev[level].nb) * kComp * pr.P;
+    f32 = pr.far_f32();
+  } else if (which == 2 || which == 3) {
+    src = which == 2 ? pr.coef : pr.pot;
+    n = size_t(pr.T) * 6;
+    f32 = pr.io_f32();
+  } else if (which == 4) {
+    src = pr.mom;
+    n = size_t(pr.nnz) * kMom;
+    f32 = pr.near_f32();
+  } else if (which == 5 || which == 6) {
+    src = which == 5 ? pr.Pi : pr.M;
+    n = size_t(pr.T) * pr.P * (which == 5 ? 1 : 3);
+    f32 = pr.far_f32();
+  } else {
+    set_error("unknown stage");
+    return PIE_ERR_PARAM;
+  }
+  if (!f32) return cuda_check(cudaMemcpy(out, src, n * sizeof(cd), cudaMemcpyDeviceToHost), "stage copy");
+  std::vector<float> tmp(2 * n);
+  s = cuda_check(cudaMemcpy(tmp.data(), src, n * sizeof(cf), cudaMemcpyDeviceToHost), "stage copy");
+  for (size_t i = 0; i < 2 * n; ++i) out[i] = tmp[i];
+  return s;
+}
+
+pie_status pie_rhs_planewave(pie_problem* h, const double khat[3], const double pol[3], double E0, void* b,
+                             int dtype, void* stream) {
+  if (!h || !khat || !pol || !b) {
+    set_error("NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  int want = h->p.io_f32() ? PIE_C64 : PIE_C128;
+  if (dtype != want) {
+    set_error("pie_rhs_planewave: dtype does not match the problem precision");
+    return PIE_ERR_PARAM;
+  }
+  return rhs_planewave(h->p, khat, pol, E0, b, static_cast<cudaStream_t>(stream));
+}
+
+pie_status pie_farfield(pie_problem* h, const void* x, const double* rhat, int64_t ndir, void* E, void* stream) {
+  if (!h || !x || !rhat || !E || ndir < 0) {
+    set_error("NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  if (ndir == 0) return PIE_OK;
+  return farfield(h->p, x, rhat, ndir, E, static_cast<cudaStream_t>(stream));
+}
+
+pie_status pie_solve(pie_problem* h, const void* b, void* x, double tol, int maxit, int restart,
+                     pie_solve_stats* stats, void* stream) {
+  if (!h || !b || !x || !(tol > 0) || maxit < 1 || restart < 1) {
+    set_error("pie_solve: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  return solve(h->p, b, x, tol, maxit, restart, stats, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

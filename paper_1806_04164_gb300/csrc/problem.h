@@ -1,0 +1,112 @@
+// Problem state shared by the host orchestration and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace pie {
+
+template <typename R>
+struct alignas(2 * sizeof(R)) C2 {
+  R x, y;
+};
+typedef C2<double> cd;
+typedef C2<float> cf;
+
+constexpr int kComp = 5;      // radiated densities per box: mu0 J (3), sigma, d
+constexpr int kNoffs = 316;   // one-box-buffer translation offsets
+constexpr int kMom = 8;       // moments per triangle pair: m0, mt(3), ms(3), mts
+constexpr int kStages = 8;    // coef, near, aggregation, interpolation, translation, anterpolation, disaggregation, assembly
+
+struct LevelDev {
+  int64_t nb = 0;
+  int32_t* il_ptr = nullptr;   // [nb+1]
+  int32_t* il_idx = nullptr;   // [nnz]
+  int32_t* il_off = nullptr;   // [nnz]
+  int32_t* child_start = nullptr;  // [nb+1] children at level l+1 (l < L)
+  int32_t* parent = nullptr;   // [nb] parent box number at level l-1
+  int8_t* octant = nullptr;    // [nb] octant of the box within its parent
+  void* trans = nullptr;       // [316][P] translation operator (far precision)
+  void* S = nullptr;           // [nb][5][P]
+  void* G = nullptr;           // [nb][5][P]
+  void* phase = nullptr;       // [8][P] interpolation phase for children (l < L)
+};
+
+struct Problem {
+  Mesh mesh;
+  Tree tree;
+  double k0 = 0, w = 0;
+  pie_params par{};
+  int P = 0;
+  int64_t T = 0, E = 0, N = 0;
+  int64_t nnz = 0;      // near pair entries
+  int64_t nleaf = 0;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+
+  // tree-ordered triangle data
+  int32_t* tri_edge = nullptr;   // [T*3]
+  double* tri_c = nullptr;       // [T*3]  s l / (2A)
+  double* tri_dcp = nullptr;     // [T*9]  c_t - p
+  int64_t* perm = nullptr;       // [T] tree -> mesh
+  int64_t* inv_perm = nullptr;   // [T] mesh -> tree
+  int32_t* edge_tt = nullptr;    // [E*2] tree positions of T+, T-
+  int8_t* edge_k = nullptr;      // [E*2] local edge slot in those triangles
+  double* vert = nullptr;        // [T*9] vertices (tree order)
+  double* cent = nullptr;        // [T*3]
+  double* h2 = nullptr;          // [T]
+  double* area = nullptr;        // [T]
+  int32_t* leaf_of = nullptr;    // [T]
+  int32_t* leaf_start = nullptr; // [nleaf+1]
+  double* leaf_center = nullptr; // [nleaf*3]
+  int32_t* near_ptr = nullptr;   // [nleaf+1]
+  int32_t* near_idx = nullptr;
+  int64_t* row_ptr = nullptr;    // [T+1]
+
+  // angular grid
+  double* khat = nullptr;        // [P*3]
+  double* wgt = nullptr;         // [P]
+  double* rule7 = nullptr;       // [7][4] barycentric (3) + weight, 7-point rule
+  double* rule64 = nullptr;      // [64][4] collapsed Gauss 8 x 8
+
+  // operator tables
+  void* mom = nullptr;           // [8][nnz] complex (near precision)
+  void* Pi = nullptr;            // [T][P]
+  void* M = nullptr;             // [T][3][P]
+  void* F = nullptr;             // [P][P]  F[p][p'] (far precision, real)
+  void* Ft = nullptr;            // [P][P]  F[p'][p]
+  std::vector<LevelDev> lev;     // [L+1]
+
+  // per-stage CUDA-event profiling (pie_profile_begin / pie_profile_end)
+  std::vector<cudaEvent_t> prof_ev;  // [max_applies][kStages][2]
+  int prof_cap = 0, prof_n = 0;
+
+  // work buffers
+  void* coef = nullptr;          // [T][6] complex (io precision)
+  void* pot = nullptr;           // [T][6]
+
+  bool near_f32() const { return par.precision != PIE_FP64; }
+  bool far_f32() const { return par.precision == PIE_FP32; }
+  bool io_f32() const { return par.precision == PIE_FP32; }
+};
+
+// setup kernels (setup.cu)
+pie_status setup_device(Problem& pr, cudaStream_t st);
+// apply (apply.cu)
+pie_status apply_one(Problem& pr, const void* x, void* y, cudaStream_t st);
+// records the start (end = false) or end of stage `stage` of the current apply when profiling
+void prof_mark(Problem& pr, int stage, bool end, cudaStream_t st);
+pie_status apply_near_one(Problem& pr, const void* x, void* y, cudaStream_t st);
+pie_status rhs_planewave(Problem& pr, const double* khat, const double* pol, double E0, void* b,
+                         cudaStream_t st);
+pie_status farfield(Problem& pr, const void* x, const double* rhat, int64_t ndir, void* E,
+                    cudaStream_t st);
+pie_status solve(Problem& pr, const void* b, void* x, double tol, int maxit, int restart,
+                 pie_solve_stats* stats, cudaStream_t st);
+
+pie_status cuda_check(cudaError_t e, const char* what);
+void* dalloc(Problem& pr, size_t bytes);
+
+}  // namespace pie
