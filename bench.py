@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rows", type=int, default=4, help="rows of the dense oracle product for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh-level", type=int, default=7,
+                    help="icosphere subdivision n (L = n levels); 7 is the timed workload, smaller for profiling")
     return ap.parse_args()
 
 
@@ -151,7 +153,8 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    xyz, tri = pi.icosphere(7)
+    nlev = args.mesh_level
+    xyz, tri = pi.icosphere(nlev)
     mesh = pg.Mesh(xyz, tri)
     k0 = 1e-3
     stream = torch.cuda.current_stream()
@@ -159,7 +162,7 @@ def run_ours(args):
     results = {}
     for mode, prec in (("mixed", pg.PIE_MIXED), ("fp64", pg.PIE_FP64)):
         t0 = time.time()
-        pr = pg.Problem(mesh, k0, 7, root_side=2.0, precision=prec)
+        pr = pg.Problem(mesh, k0, nlev, root_side=2.0, precision=prec)
         setup_s = time.time() - t0
         x = torch.from_numpy(x_host).to(pr.torch_dtype).cuda()
         y = torch.empty_like(x)
@@ -242,7 +245,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "c64 near + c128 far (mixed)",
         "data": "synthetic (icosphere mesh, seeded complex-normal x)",
-        "config": dict(WORKLOAD, precision="mixed", parallelism=f"replicas{world}",
+        "config": dict(WORKLOAD if nlev == 7 else dict(workload=f"pec_sphere_icosphere{nlev}", N=pr.N, levels=pr.L),
+                       precision="mixed", parallelism=f"replicas{world}",
                        l2="working set > L2 (near moments %.1f GB), no flush" % (main["near_pairs"] * 64 / 1e9)),
         "e2e": {"value": world * K / (main["e2e_ms"] * 1e-3), "unit": "matvecs/s",
                 "h2d_bytes_per_step": main["bytes_io"], "d2h_bytes_per_step": main["bytes_io"]},
@@ -257,7 +261,7 @@ def run_ours(args):
         "device_bytes": main["device_bytes"],
         "clocks": main["clocks"],
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and nlev == 7:
         line["cpu_baseline"] = cpu_baseline(args.cpu_rows)
     print(json.dumps(line))
 
