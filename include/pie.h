@@ -159,6 +159,25 @@ pie_status pie_apply(pie_problem* pr, const void* x, void* y, int nrhs, int dtyp
  * as a sparse preconditioner and for checking the near part by itself. */
 pie_status pie_apply_near(pie_problem* pr, const void* x, void* y, int nrhs, int dtype, void* stream);
 
+/* Allocation-free variant of pie_apply_near (the paper has no counterpart:
+ * this serves callers that cannot allocate device memory when they need a
+ * product -- code inside a CUDA-graph capture they do not own, hosts that
+ * forbid allocation after start-up, frameworks whose allocator owns all
+ * device memory).  Computes y = Z_near x for one right-hand side (x, y:
+ * device, N complex of the problem's dtype) and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Its per-triangle scratch (local
+ * coefficients and potentials, 2 x 6 complex per triangle) lives in one
+ * fixed 24 MiB device array inside the library, which every GPU that loads
+ * the library holds until the process exits; meshes above 131072 triangles
+ * (complex double) or 262144 (complex float) are rejected with
+ * PIE_ERR_PARAM.  The first call on a device looks the array's device
+ * address up (cudaGetSymbolAddress) and must come before any stream capture
+ * on that device.  All calls share the array and every call overwrites the
+ * parts it reads, so nothing carries over between calls; calls that overlap
+ * on the GPU (different streams, or different problems at once) race on
+ * it.  Errors: PIE_ERR_PARAM, PIE_ERR_CUDA. */
+pie_status pie_apply_near_noalloc(pie_problem* pr, const void* x, void* y, int dtype, void* stream);
+
 /* Per-stage timing of products (CUDA events recorded on the apply stream
  * around each stage).  pie_profile_begin arms recording for the next
  * max_applies single-column products; pie_profile_end waits for them and

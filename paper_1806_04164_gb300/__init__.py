@@ -50,7 +50,7 @@ _lib = None
 EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_destroy", "pie_mesh_info",
            "pie_mesh_edges", "pie_problem_create", "pie_problem_destroy", "pie_problem_info", "pie_problem_perm",
            "pie_problem_level", "pie_problem_near", "pie_apply", "pie_apply_near", "pie_problem_stage", "pie_rhs_planewave",
-           "pie_farfield", "pie_solve", "pie_profile_begin", "pie_profile_end"]
+           "pie_farfield", "pie_solve", "pie_profile_begin", "pie_profile_end", "pie_apply_near_noalloc"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -80,6 +80,7 @@ def lib():
         L.pie_problem_near.argtypes = [vp, P64, P64, P64]
         L.pie_apply.argtypes = [vp, vp, vp, i32, i32, vp]
         L.pie_apply_near.argtypes = [vp, vp, vp, i32, i32, vp]
+        L.pie_apply_near_noalloc.argtypes = [vp, vp, vp, i32, vp]
         L.pie_problem_stage.argtypes = [vp, i32, i32, PD, vp]
         L.pie_rhs_planewave.argtypes = [vp, PD, PD, dbl, vp, i32, vp]
         L.pie_farfield.argtypes = [vp, vp, PD, i64, vp, vp]

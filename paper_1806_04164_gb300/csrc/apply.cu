@@ -559,3 +559,37 @@ pie_status farfield(Problem& pr, const void* x, const double* rhat, int64_t ndir
 }
 
 }  // namespace pie
+
+namespace pie {
+
+// Near part with caller-chosen scratch for the per-triangle coefficients and
+// potentials (each [T][6] complex of the problem's io type).
+pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, void* pot, cudaStream_t st) {
+  const double w2e = pr.w * pr.w * eps0();
+  if (pr.io_f32()) {
+    k_coef<float><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cf*>(x), pr.perm, pr.tri_edge,
+                                                   pr.tri_c, pr.tri_dcp, w2e, static_cast<cf*>(coef));
+    k_near<float, float><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
+                                                               pr.near_idx, pr.row_ptr, static_cast<const cf*>(pr.mom),
+                                                               static_cast<const cf*>(coef), float(kMu0),
+                                                               static_cast<cf*>(pot));
+    k_assemble<float><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                       pr.inv_perm, static_cast<const cf*>(pot), static_cast<cf*>(y));
+  } else {
+    k_coef<double><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cd*>(x), pr.perm, pr.tri_edge,
+                                                    pr.tri_c, pr.tri_dcp, w2e, static_cast<cd*>(coef));
+    if (pr.near_f32())
+      k_near<float, double><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
+          pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.row_ptr,
+          static_cast<const cf*>(pr.mom), static_cast<const cd*>(coef), float(kMu0), static_cast<cd*>(pot));
+    else
+      k_near<double, double><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
+          pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.row_ptr,
+          static_cast<const cd*>(pr.mom), static_cast<const cd*>(coef), kMu0, static_cast<cd*>(pot));
+    k_assemble<double><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                        pr.inv_perm, static_cast<const cd*>(pot), static_cast<cd*>(y));
+  }
+  return cuda_check(cudaGetLastError(), "apply_near_noalloc launch");
+}
+
+}  // namespace pie

@@ -99,6 +99,7 @@ pie_status apply_one(Problem& pr, const void* x, void* y, cudaStream_t st);
 // records the start (end = false) or end of stage `stage` of the current apply when profiling
 void prof_mark(Problem& pr, int stage, bool end, cudaStream_t st);
 pie_status apply_near_one(Problem& pr, const void* x, void* y, cudaStream_t st);
+pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, void* pot, cudaStream_t st);
 pie_status rhs_planewave(Problem& pr, const double* khat, const double* pol, double E0, void* b,
                          cudaStream_t st);
 pie_status farfield(Problem& pr, const void* x, const double* rhat, int64_t ndir, void* E,
