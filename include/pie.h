@@ -79,8 +79,8 @@ typedef struct {
   int tau;           /* truncation number of Eq. (5) */
   double kappa_a;    /* x = (k0 / s_l) a_l, the same at every level, so the
                         scale factor of Eq. (4) is s_l = k0 a_l / x */
-  int ntheta;        /* angular samples: ntheta Gauss-Legendre nodes in
-                        cos(theta) x 2 ntheta azimuths, P = 2 ntheta^2 */
+  int ntheta;        /* angular samples: ntheta (even) Gauss-Legendre nodes
+                        in cos(theta) x 2 ntheta azimuths, P = 2 ntheta^2 */
   int precision;     /* pie_precision */
 } pie_params;
 
@@ -198,8 +198,9 @@ pie_status pie_profile_end(pie_problem* pr, double* stage_ms, int32_t* applies);
  * 3 = per-triangle potentials [T][6] (U, V_x, V_y, V_z, T1, T2), 4 = near
  * pair moments [8][nnz] (m0, mt_xyz, ms_xyz, mts; entries ordered by test
  * triangle in tree order, then by near box, then by source triangle),
- * 5 = leaf radiation table Pi [T][P], 6 = leaf radiation table M [T][3][P]
- * (tree order).  Patterns
+ * 5 = leaf radiation table Pi [T][P/2], 6 = leaf radiation table M
+ * [T][3][P/2] (tree order; the half grid of theta rows 0..ntheta/2-1, the
+ * other half being the complex conjugates at the antipodes).  Patterns
  * are [nb][5][P] complex double (converted from float in PIE_FP32). */
 pie_status pie_problem_stage(pie_problem* pr, int which, int level, double* out, void* stream);
 

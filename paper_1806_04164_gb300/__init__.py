@@ -224,11 +224,11 @@ class Problem:
             n = 8 * self.near_pairs
             shape = (8, self.near_pairs)
         elif which == 5:
-            n = self.T * self.P
-            shape = (self.T, self.P)
+            n = self.T * self.P // 2
+            shape = (self.T, self.P // 2)
         elif which == 6:
-            n = self.T * 3 * self.P
-            shape = (self.T, 3, self.P)
+            n = self.T * 3 * self.P // 2
+            shape = (self.T, 3, self.P // 2)
         else:
             n = self.T * 6
             shape = (self.T, 6)

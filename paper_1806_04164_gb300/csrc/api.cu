@@ -96,7 +96,8 @@ pie_status pie_problem_create(const pie_mesh* m, double k0, const pie_params* pa
   }
   *out = nullptr;
   if (!(k0 > 0) || par->levels < 3 || par->levels > 21 || par->tau < 0 || par->tau > 30 || par->ntheta < 1 ||
-      2 * par->ntheta * par->ntheta > 1024 || !(par->kappa_a > 0) || par->precision < 0 || par->precision > 2) {
+      2 * par->ntheta * par->ntheta > 1024 || (par->ntheta & 1) || !(par->kappa_a > 0) || par->precision < 0 ||
+      par->precision > 2) {
     set_error("pie_problem_create: parameter out of range");
     return PIE_ERR_PARAM;
   }
@@ -314,7 +315,7 @@ pie_status pie_problem_stage(pie_problem* h, int which, int level, double* out, 
     f32 = pr.near_f32();
   } else if (which == 5 || which == 6) {
     src = which == 5 ? pr.Pi : pr.M;
-    n = size_t(pr.T) * pr.P * (which == 5 ? 1 : 3);
+    n = size_t(pr.T) * (pr.P / 2) * (which == 5 ? 1 : 3);
     f32 = pr.far_f32();
   } else {
     set_error("unknown stage");

@@ -13,7 +13,8 @@ namespace pie {
 template <typename Rio>
 __global__ void k_coef(int64_t T, int64_t E, const C2<Rio>* __restrict__ x, const int64_t* __restrict__ perm,
                        const int32_t* __restrict__ tri_edge, const double* __restrict__ tri_c,
-                       const double* __restrict__ tri_dcp, double w2e, C2<Rio>* __restrict__ coef) {
+                       const double* __restrict__ tri_dcp, double w2e, C2<Rio>* __restrict__ coef,
+                       cf* __restrict__ coef32) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= T) return;
   double ar = 0, ai = 0, br[3] = {0, 0, 0}, bi[3] = {0, 0, 0};
@@ -34,11 +35,15 @@ __global__ void k_coef(int64_t T, int64_t E, const C2<Rio>* __restrict__ x, cons
   }
   C2<Rio> s = x[E + perm[t]];
   double sr = double(s.x), si = double(s.y);
-  C2<Rio>* o = coef + 6 * t;
-  o[0] = mk<Rio>(Rio(ar), Rio(ai));
-  for (int d = 0; d < 3; ++d) o[1 + d] = mk<Rio>(Rio(br[d]), Rio(bi[d]));
-  o[4] = s;
-  o[5] = mk<Rio>(Rio(2.0 * ar + w2e * sr), Rio(2.0 * ai + w2e * si));
+  double v[12] = {ar, ai, br[0], bi[0], br[1], bi[1], br[2], bi[2], sr, si, 2.0 * ar + w2e * sr, 2.0 * ai + w2e * si};
+  if (coef) {
+    C2<Rio>* o = coef + 6 * t;
+    for (int q = 0; q < 6; ++q) o[q] = mk<Rio>(Rio(v[2 * q]), Rio(v[2 * q + 1]));
+  }
+  if (coef32) {  // float copy for a float near part: converted once per triangle
+    cf* o = coef32 + 6 * t;
+    for (int q = 0; q < 6; ++q) o[q] = mk<float>(float(v[2 * q]), float(v[2 * q + 1]));
+  }
 }
 
 // a1: near part.  One warp per test triangle t; lanes run over the source
@@ -51,7 +56,7 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
                                               const int32_t* __restrict__ near_ptr,
                                               const int32_t* __restrict__ near_idx,
                                               const int64_t* __restrict__ row_ptr, const C2<Rm>* __restrict__ mom,
-                                              const C2<Rio>* __restrict__ coef, Rm mu0, C2<Rio>* __restrict__ pot) {
+                                              const C2<Rm>* __restrict__ coef, Rm mu0, C2<Rio>* __restrict__ pot) {
   int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (t >= T) return;
@@ -64,9 +69,8 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
     int ns = leaf_start[q + 1] - s0;
     for (int j = lane; j < ns; j += 32) {
       int64_t ee = e + j;
-      const C2<Rio>* c = coef + 6 * (int64_t)(s0 + j);
-      C2<Rm> a = cvt<Rm>(c[0]), b0 = cvt<Rm>(c[1]), b1 = cvt<Rm>(c[2]), b2 = cvt<Rm>(c[3]);
-      C2<Rm> sg = cvt<Rm>(c[4]), dd = cvt<Rm>(c[5]);
+      const C2<Rm>* c = coef + 6 * (int64_t)(s0 + j);
+      C2<Rm> a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
       C2<Rm> m0 = mom[ee];
       C2<Rm> mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
       C2<Rm> ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
@@ -101,38 +105,56 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
   }
 }
 
-// a2: leaf aggregation.  One block per leaf box, one thread per angular
-// sample p: S[b][c][p] = sum_t rho_c radiation patterns (Pi, M tables).
-template <typename Rf, typename Rio>
-__global__ void k_agg(int P, const int32_t* __restrict__ leaf_start, const C2<Rf>* __restrict__ Pi,
-                      const C2<Rf>* __restrict__ M, const C2<Rio>* __restrict__ coef, Rf mu0,
+// Antipode of half-grid sample q (theta rows 0..ntheta/2-1): -khat_q is
+// the sample (ntheta-1-i, j+ntheta mod 2 ntheta).
+__device__ __forceinline__ int antipode(int q, int ntheta) {
+  int nphi = 2 * ntheta;
+  int i = q / nphi, j = q % nphi;
+  return (ntheta - 1 - i) * nphi + (j + ntheta) % nphi;
+}
+
+// a2: leaf aggregation.  One block per leaf box, one thread per half-grid
+// sample q.  The radiation tables are stored for the half grid only, since
+// Pi(-khat) = conj(Pi(khat)) and M(-khat) = conj(M(khat)); with c X = c Xr +
+// i c Xi the pair of samples is S(q) = A + iB, S(-q) = A - iB, where
+// A = sum c Xr and B = sum c Xi.
+template <typename Rf>
+__global__ void k_agg(int P, int ntheta, const int32_t* __restrict__ leaf_start, const C2<Rf>* __restrict__ Pi,
+                      const C2<Rf>* __restrict__ M, const C2<Rf>* __restrict__ coef, Rf mu0,
                       C2<Rf>* __restrict__ S) {
-  int b = blockIdx.x;
-  int t0 = leaf_start[b], t1 = leaf_start[b + 1];
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    C2<Rf> s0 = mk<Rf>(0, 0), s1 = s0, s2 = s0, s3 = s0, s4 = s0;
+  const int b = blockIdx.x;
+  const int Ph = P / 2;
+  const int t0 = leaf_start[b], t1 = leaf_start[b + 1];
+  for (int q = threadIdx.x; q < Ph; q += blockDim.x) {
+    C2<Rf> A[kComp], B[kComp];
+#pragma unroll
+    for (int c = 0; c < kComp; ++c) A[c] = B[c] = mk<Rf>(0, 0);
     for (int t = t0; t < t1; ++t) {
-      const C2<Rio>* c = coef + 6 * (int64_t)t;
-      C2<Rf> a = cvt<Rf>(c[0]);
-      C2<Rf> pi = Pi[(int64_t)t * P + p];
-      C2<Rf> m0 = M[((int64_t)t * 3 + 0) * P + p];
-      C2<Rf> m1 = M[((int64_t)t * 3 + 1) * P + p];
-      C2<Rf> m2 = M[((int64_t)t * 3 + 2) * P + p];
-      cfma(s0, a, m0);
-      cfma(s0, cvt<Rf>(c[1]), pi);
-      cfma(s1, a, m1);
-      cfma(s1, cvt<Rf>(c[2]), pi);
-      cfma(s2, a, m2);
-      cfma(s2, cvt<Rf>(c[3]), pi);
-      cfma(s3, cvt<Rf>(c[4]), pi);
-      cfma(s4, cvt<Rf>(c[5]), pi);
+      const C2<Rf>* cf_ = coef + 6 * (int64_t)t;
+      C2<Rf> a = cf_[0];
+      C2<Rf> pi = Pi[(int64_t)t * Ph + q];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        C2<Rf> m = M[((int64_t)t * 3 + d) * Ph + q];
+        C2<Rf> be = cf_[1 + d];
+        rfma(A[d], m.x, a);
+        rfma(A[d], pi.x, be);
+        rfma(B[d], m.y, a);
+        rfma(B[d], pi.y, be);
+      }
+      rfma(A[3], pi.x, cf_[4]);
+      rfma(B[3], pi.y, cf_[4]);
+      rfma(A[4], pi.x, cf_[5]);
+      rfma(B[4], pi.y, cf_[5]);
     }
-    C2<Rf>* o = S + (int64_t)b * kComp * P + p;
-    o[0] = mk<Rf>(mu0 * s0.x, mu0 * s0.y);
-    o[P] = mk<Rf>(mu0 * s1.x, mu0 * s1.y);
-    o[2 * P] = mk<Rf>(mu0 * s2.x, mu0 * s2.y);
-    o[3 * P] = s3;
-    o[4 * P] = s4;
+    const int qa = antipode(q, ntheta);
+    C2<Rf>* o = S + (int64_t)b * kComp * P;
+#pragma unroll
+    for (int c = 0; c < kComp; ++c) {
+      Rf f = c < 3 ? mu0 : Rf(1);
+      o[c * P + q] = mk<Rf>(f * (A[c].x - B[c].y), f * (A[c].y + B[c].x));
+      o[c * P + qa] = mk<Rf>(f * (A[c].x + B[c].y), f * (A[c].y - B[c].x));
+    }
   }
 }
 
@@ -171,6 +193,205 @@ __global__ void k_interp(int P, const int32_t* __restrict__ child_start, const i
   if (p < P) {
 #pragma unroll
     for (int c = 0; c < kComp; ++c) Sp[((int64_t)b * kComp + c) * P + p] = acc[c];
+  }
+}
+
+// ---- factorised filter: F is block-circulant in azimuth (its entries depend
+// on phi_j - phi_j' only), so the length-NPHI DFT along phi turns it into
+// one real NT x NT block K_m per azimuthal frequency m:
+//   (F s)[i][j] = sum_m e^{i m phi_j} sum_i' K_m[i][i'] shat[i'][m],
+//   shat[i'][m] = sum_j e^{-i m phi_j} s[i'][j],  K_m = (1/NPHI) DFT_d f_ii'(d).
+// F^T uses K_m transposed.
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+__host__ __device__ constexpr int bitrev(int x, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+// In-register radix-2 FFT; tw[k] = exp(-2 pi i k / N), k < N/2.  Forward
+// uses tw, inverse its conjugate (no 1/N scaling).
+template <int N, typename R>
+__device__ __forceinline__ void fft_reg(C2<R>* x, const C2<R>* tw, bool inverse) {
+  constexpr int LG = ilog2c(N);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int j = bitrev(i, LG);
+    if (j > i) {
+      C2<R> t = x[i];
+      x[i] = x[j];
+      x[j] = t;
+    }
+  }
+#pragma unroll
+  for (int len = 2; len <= N; len <<= 1) {
+    const int half = len >> 1, step = N / len;
+#pragma unroll
+    for (int i = 0; i < N; i += len) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        C2<R> w = tw[k * step];
+        if (inverse) w.y = -w.y;
+        C2<R> u = x[i + k], v = cmul(x[i + k + half], w);
+        x[i + k] = mk<R>(u.x + v.x, u.y + v.y);
+        x[i + k + half] = mk<R>(u.x - v.x, u.y - v.y);
+      }
+    }
+  }
+}
+
+constexpr int kFftBatch = 4;  // children per batch in the factorised filter kernels
+
+// a3 (factorised): one block per parent box, kFftBatch children at a time,
+// one thread per (child, component, theta row).
+template <int NT, typename Rf>
+__global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
+    const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Sc,
+    const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Sp) {
+  constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);  // spectra [slot][c][m][i], then results [slot][c][p]
+  C2<Rf>* B = A + NB * kComp * P;                     // filtered spectra [slot][c][i][m]
+  C2<Rf>* acc = B + NB * kComp * P;                   // parent pattern [c][p]
+  C2<Rf>* tw = acc + kComp * P;                       // twiddles
+  Rf* K = reinterpret_cast<Rf*>(tw + NPHI / 2);       // K_m blocks
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < NPHI * NT * NT; i += nth) K[i] = Kf[i];
+  for (int i = tid; i < kComp * P; i += nth) acc[i] = mk<Rf>(0, 0);
+  if (tid < NPHI / 2) {
+    Rf sn, cs;
+    sincospi(Rf(2 * tid) / Rf(NPHI), &sn, &cs);
+    tw[tid] = mk<Rf>(cs, -sn);
+  }
+  const int b = blockIdx.x, c0 = child_start[b], c1 = child_start[b + 1];
+  for (int base = c0; base < c1; base += NB) {
+    const int nb = min(NB, c1 - base);
+    __syncthreads();
+    {  // forward DFT of every row
+      const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
+      if (slot < nb) {
+        C2<Rf> x[NPHI];
+        const C2<Rf>* src = Sc + ((int64_t)(base + slot) * kComp + c) * P + i * NPHI;
+#pragma unroll
+        for (int j = 0; j < NPHI; ++j) x[j] = src[j];
+        fft_reg<NPHI>(x, tw, false);
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * NT + i] = x[m];
+      }
+    }
+    __syncthreads();
+    for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // K_m blocks
+      const int sc = it / NPHI, m = it % NPHI;
+      const C2<Rf>* a = A + (sc * NPHI + m) * NT;
+      const Rf* Km = K + m * NT * NT;
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        C2<Rf> t = mk<Rf>(0, 0);
+#pragma unroll
+        for (int k = 0; k < NT; ++k) rfma(t, Km[i * NT + k], a[k]);
+        B[(sc * NT + i) * NPHI + m] = t;
+      }
+    }
+    __syncthreads();
+    {  // inverse DFT, phase shift to the parent centre
+      const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
+      if (slot < nb) {
+        C2<Rf> x[NPHI];
+        const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * NPHI;
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) x[m] = src[m];
+        fft_reg<NPHI>(x, tw, true);
+        const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
+        C2<Rf>* dst = A + (slot * kComp + c) * P + i * NPHI;
+#pragma unroll
+        for (int j = 0; j < NPHI; ++j) dst[j] = cmul(ph[j], x[j]);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < kComp * P; i += nth) {
+      C2<Rf> v = acc[i];
+      for (int slot = 0; slot < nb; ++slot) {
+        C2<Rf> u = A[slot * kComp * P + i];
+        v.x += u.x;
+        v.y += u.y;
+      }
+      acc[i] = v;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < kComp * P; i += nth) Sp[(int64_t)b * kComp * P + i] = acc[i];
+}
+
+// a5 (factorised): one block per parent box; its children take
+// F^T (conj(phase_o) G_parent), added to their incoming patterns.
+template <int NT, typename Rf>
+__global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
+    const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Gp,
+    const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Gc) {
+  constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);
+  C2<Rf>* B = A + NB * kComp * P;
+  C2<Rf>* tw = B + NB * kComp * P;
+  Rf* K = reinterpret_cast<Rf*>(tw + NPHI / 2);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < NPHI * NT * NT; i += nth) K[i] = Kf[i];
+  if (tid < NPHI / 2) {
+    Rf sn, cs;
+    sincospi(Rf(2 * tid) / Rf(NPHI), &sn, &cs);
+    tw[tid] = mk<Rf>(cs, -sn);
+  }
+  const int b = blockIdx.x, c0 = child_start[b], c1 = child_start[b + 1];
+  for (int base = c0; base < c1; base += NB) {
+    const int nb = min(NB, c1 - base);
+    __syncthreads();
+    {
+      const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
+      if (slot < nb) {
+        C2<Rf> x[NPHI];
+        const C2<Rf>* src = Gp + ((int64_t)b * kComp + c) * P + i * NPHI;
+        const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
+#pragma unroll
+        for (int j = 0; j < NPHI; ++j) {
+          C2<Rf> g = src[j], w = ph[j];
+          x[j] = mk<Rf>(w.x * g.x + w.y * g.y, w.x * g.y - w.y * g.x);  // conj(w) g
+        }
+        fft_reg<NPHI>(x, tw, false);
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * NT + i] = x[m];
+      }
+    }
+    __syncthreads();
+    for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // transposed K_m blocks
+      const int sc = it / NPHI, m = it % NPHI;
+      const C2<Rf>* a = A + (sc * NPHI + m) * NT;
+      const Rf* Km = K + m * NT * NT;
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        C2<Rf> t = mk<Rf>(0, 0);
+#pragma unroll
+        for (int k = 0; k < NT; ++k) rfma(t, Km[k * NT + i], a[k]);
+        B[(sc * NT + i) * NPHI + m] = t;
+      }
+    }
+    __syncthreads();
+    {
+      const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
+      if (slot < nb) {
+        C2<Rf> x[NPHI];
+        const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * NPHI;
+#pragma unroll
+        for (int m = 0; m < NPHI; ++m) x[m] = src[m];
+        fft_reg<NPHI>(x, tw, true);
+        C2<Rf>* dst = Gc + ((int64_t)(base + slot) * kComp + c) * P + i * NPHI;
+#pragma unroll
+        for (int j = 0; j < NPHI; ++j) {
+          C2<Rf> g = dst[j];
+          dst[j] = mk<Rf>(g.x + x[j].x, g.y + x[j].y);
+        }
+      }
+    }
   }
 }
 
@@ -237,30 +458,50 @@ __global__ void k_anterp(int P, const int32_t* __restrict__ parent, const int8_t
 }
 
 // a6: leaf disaggregation with the receiving (conjugate) patterns; one warp
-// per triangle, lanes over samples; adds to pot[t].
+// per triangle, lanes over half-grid samples.  Over a sample pair (q, -q):
+// conj(X(q)) G(q) + X(q) G(-q) = Xr (G(q) + G(-q)) - i Xi (G(q) - G(-q)).
+// Adds to pot[t].
 template <typename Rf, typename Rio>
-__global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, const int32_t* __restrict__ leaf_of,
+__global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, int ntheta, const int32_t* __restrict__ leaf_of,
                                                 const C2<Rf>* __restrict__ Pi, const C2<Rf>* __restrict__ M,
                                                 const C2<Rf>* __restrict__ G, C2<Rio>* __restrict__ pot) {
   int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (t >= T) return;
+  const int Ph = P / 2;
   const C2<Rf>* g = G + (int64_t)leaf_of[t] * kComp * P;
-  C2<Rf> U = mk<Rf>(0, 0), V0 = U, V1 = U, V2 = U, T1 = U, T2 = U;
-  for (int p = lane; p < P; p += 32) {
-    C2<Rf> pi = Pi[t * P + p];
-    C2<Rf> m0 = M[(t * 3 + 0) * P + p], m1 = M[(t * 3 + 1) * P + p], m2 = M[(t * 3 + 2) * P + p];
-    C2<Rf> g0 = g[p], g1 = g[P + p], g2 = g[2 * P + p], g3 = g[3 * P + p], g4 = g[4 * P + p];
-    cfma_conj(U, m0, g0);
-    cfma_conj(U, m1, g1);
-    cfma_conj(U, m2, g2);
-    cfma_conj(V0, pi, g0);
-    cfma_conj(V1, pi, g1);
-    cfma_conj(V2, pi, g2);
-    cfma_conj(T1, pi, g3);
-    cfma_conj(T2, pi, g4);
+  C2<Rf> acc[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) acc[i] = mk<Rf>(0, 0);
+  for (int q = lane; q < Ph; q += 32) {
+    const int qa = antipode(q, ntheta);
+    C2<Rf> gs[kComp], gd[kComp];
+#pragma unroll
+    for (int c = 0; c < kComp; ++c) {
+      C2<Rf> u = g[c * P + q], v = g[c * P + qa];
+      gs[c] = mk<Rf>(u.x + v.x, u.y + v.y);
+      gd[c] = mk<Rf>(u.x - v.x, u.y - v.y);
+    }
+    C2<Rf> pi = Pi[t * Ph + q];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      C2<Rf> m = M[(t * 3 + d) * Ph + q];
+      // U += Mr gs - i Mi gd
+      rfma(acc[0], m.x, gs[d]);
+      acc[0].x = fma(m.y, gd[d].y, acc[0].x);
+      acc[0].y = fma(-m.y, gd[d].x, acc[0].y);
+      // V_d += Pr gs - i Pi gd
+      rfma(acc[1 + d], pi.x, gs[d]);
+      acc[1 + d].x = fma(pi.y, gd[d].y, acc[1 + d].x);
+      acc[1 + d].y = fma(-pi.y, gd[d].x, acc[1 + d].y);
+    }
+#pragma unroll
+    for (int c = 3; c < 5; ++c) {
+      rfma(acc[1 + c], pi.x, gs[c]);
+      acc[1 + c].x = fma(pi.y, gd[c].y, acc[1 + c].x);
+      acc[1 + c].y = fma(-pi.y, gd[c].x, acc[1 + c].y);
+    }
   }
-  C2<Rf> acc[6] = {U, V0, V1, V2, T1, T2};
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     acc[i].x = warp_sum(acc[i].x);
@@ -315,6 +556,29 @@ void prof_mark(Problem& pr, int stage, bool end, cudaStream_t st) {
   cudaEventRecord(pr.prof_ev[(size_t(pr.prof_n) * kStages + stage) * 2 + (end ? 1 : 0)], st);
 }
 
+template <int NT, typename Rf>
+static size_t fft_smem(bool interp) {
+  constexpr int NPHI = 2 * NT, P = NT * NPHI;
+  return sizeof(C2<Rf>) * (2 * kFftBatch * kComp * P + (interp ? kComp * P : 0) + NPHI / 2) +
+         sizeof(Rf) * NPHI * NT * NT;
+}
+
+// Opt the factorised filter kernels into their (above 48 KB) dynamic shared memory.
+template <int NT, typename Rf>
+static pie_status fft_prepare() {
+  static bool done = false;
+  if (done) return PIE_OK;
+  pie_status s = cuda_check(cudaFuncSetAttribute(k_interp_fft<NT, Rf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(fft_smem<NT, Rf>(true))),
+                            "smem attribute");
+  if (s == PIE_OK)
+    s = cuda_check(cudaFuncSetAttribute(k_anterp_fft<NT, Rf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(fft_smem<NT, Rf>(false))),
+                   "smem attribute");
+  done = s == PIE_OK;
+  return s;
+}
+
 template <typename Rm, typename Rf, typename Rio>
 static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st) {
   const int P = pr.P;
@@ -324,25 +588,40 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st
   C2<Rio>* coef = static_cast<C2<Rio>*>(pr.coef);
   C2<Rio>* pot = static_cast<C2<Rio>*>(pr.pot);
   const double w2e = pr.w * pr.w * eps0();
+  constexpr bool split = sizeof(Rm) < sizeof(Rio);  // float near part, double coefficients
+  cf* coef32 = split ? static_cast<cf*>(pr.coef32) : nullptr;
+  const C2<Rm>* ncoef = split ? reinterpret_cast<const C2<Rm>*>(coef32) : reinterpret_cast<const C2<Rm>*>(coef);
   prof_mark(pr, 0, false, st);
   k_coef<Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, x, pr.perm, pr.tri_edge, pr.tri_c, pr.tri_dcp, w2e,
-                                               coef);
+                                               coef, coef32);
   prof_mark(pr, 0, true, st);
   prof_mark(pr, 1, false, st);
   k_near<Rm, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
                                                         pr.near_idx, pr.row_ptr,
-                                                        static_cast<const C2<Rm>*>(pr.mom), coef, Rm(kMu0), pot);
+                                                        static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot);
   prof_mark(pr, 1, true, st);
   const int tpb = P < 1024 ? ((P + 31) / 32) * 32 : 1024;
   const C2<Rf>* Pi = static_cast<const C2<Rf>*>(pr.Pi);
   const C2<Rf>* M = static_cast<const C2<Rf>*>(pr.M);
   prof_mark(pr, 2, false, st);
-  k_agg<Rf, Rio><<<unsigned(pr.lev[L].nb), tpb, 0, st>>>(P, pr.leaf_start, Pi, M, coef, Rf(kMu0),
-                                                        static_cast<C2<Rf>*>(pr.lev[L].S));
+  // far coefficients in the far precision (MIXED and FP64: the io buffer)
+  const C2<Rf>* fcoef = reinterpret_cast<const C2<Rf>*>(sizeof(Rf) == sizeof(Rio) ? (const void*)coef : pr.coef32);
+  k_agg<Rf><<<unsigned(pr.lev[L].nb), ((P / 2 + 31) / 32) * 32, 0, st>>>(P, pr.par.ntheta, pr.leaf_start, Pi, M, fcoef,
+                                                                       Rf(kMu0), static_cast<C2<Rf>*>(pr.lev[L].S));
   prof_mark(pr, 2, true, st);
   const size_t sm = sizeof(C2<Rf>) * kComp * P;
+  const bool fft8 = pr.par.ntheta == 8;
+  if (fft8) {
+    pie_status s = fft_prepare<8, Rf>();
+    if (s != PIE_OK) return s;
+  }
   prof_mark(pr, 3, false, st);
-  for (int l = L - 1; l >= 3; --l) {
+  for (int l = L - 1; l >= 3 && fft8; --l) {
+    k_interp_fft<8, Rf><<<unsigned(pr.lev[l].nb), kFftBatch * kComp * 8, fft_smem<8, Rf>(true), st>>>(
+        pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
+        static_cast<const Rf*>(pr.Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l].S));
+  }
+  for (int l = L - 1; l >= 3 && !fft8; --l) {
     k_interp<Rf><<<unsigned(pr.lev[l].nb), tpb, sm, st>>>(
         P, pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
         static_cast<const Rf*>(pr.Ft), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l].S));
@@ -357,14 +636,19 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st
   }
   prof_mark(pr, 4, true, st);
   prof_mark(pr, 5, false, st);
-  for (int l = 3; l < L; ++l) {
+  for (int l = 3; l < L && fft8; ++l) {
+    k_anterp_fft<8, Rf><<<unsigned(pr.lev[l].nb), kFftBatch * kComp * 8, fft_smem<8, Rf>(false), st>>>(
+        pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
+        static_cast<const Rf*>(pr.Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l + 1].G));
+  }
+  for (int l = 3; l < L && !fft8; ++l) {
     k_anterp<Rf><<<unsigned(pr.lev[l + 1].nb), tpb, sm, st>>>(
         P, pr.lev[l + 1].parent, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
         static_cast<const Rf*>(pr.F), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l + 1].G));
   }
   prof_mark(pr, 5, true, st);
   prof_mark(pr, 6, false, st);
-  k_disagg<Rf, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, P, pr.leaf_of, Pi, M,
+  k_disagg<Rf, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, P, pr.par.ntheta, pr.leaf_of, Pi, M,
                                                          static_cast<const C2<Rf>*>(pr.lev[L].G), pot);
   prof_mark(pr, 6, true, st);
   prof_mark(pr, 7, false, st);
@@ -380,11 +664,14 @@ template <typename Rm, typename Rio>
 static pie_status apply_near_t(Problem& pr, const void* xv, void* yv, cudaStream_t st) {
   C2<Rio>* coef = static_cast<C2<Rio>*>(pr.coef);
   C2<Rio>* pot = static_cast<C2<Rio>*>(pr.pot);
+  constexpr bool split = sizeof(Rm) < sizeof(Rio);
+  cf* coef32 = split ? static_cast<cf*>(pr.coef32) : nullptr;
+  const C2<Rm>* ncoef = split ? reinterpret_cast<const C2<Rm>*>(coef32) : reinterpret_cast<const C2<Rm>*>(coef);
   k_coef<Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const C2<Rio>*>(xv), pr.perm, pr.tri_edge,
-                                               pr.tri_c, pr.tri_dcp, pr.w * pr.w * eps0(), coef);
+                                               pr.tri_c, pr.tri_dcp, pr.w * pr.w * eps0(), coef, coef32);
   k_near<Rm, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
                                                         pr.near_idx, pr.row_ptr,
-                                                        static_cast<const C2<Rm>*>(pr.mom), coef, Rm(kMu0), pot);
+                                                        static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot);
   k_assemble<Rio><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                    pr.inv_perm, pot, static_cast<C2<Rio>*>(yv));
   return cuda_check(cudaGetLastError(), "apply_near launch");
@@ -544,12 +831,12 @@ pie_status farfield(Problem& pr, const void* x, const double* rhat, int64_t ndir
   const double pref = pr.w * kMu0 / (4.0 * kPi);
   if (pr.io_f32()) {
     k_coef<float><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cf*>(x), pr.perm, pr.tri_edge,
-                                                   pr.tri_c, pr.tri_dcp, w2e, static_cast<cf*>(pr.coef));
+                                                   pr.tri_c, pr.tri_dcp, w2e, static_cast<cf*>(pr.coef), nullptr);
     k_farfield<float><<<unsigned(ndir), 256, 0, st>>>(pr.T, pr.vert, pr.cent, pr.area, static_cast<cf*>(pr.coef),
                                                       d_rhat, pr.k0, pref, rule, static_cast<cd*>(E));
   } else {
     k_coef<double><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cd*>(x), pr.perm, pr.tri_edge,
-                                                    pr.tri_c, pr.tri_dcp, w2e, static_cast<cd*>(pr.coef));
+                                                    pr.tri_c, pr.tri_dcp, w2e, static_cast<cd*>(pr.coef), nullptr);
     k_farfield<double><<<unsigned(ndir), 256, 0, st>>>(pr.T, pr.vert, pr.cent, pr.area, static_cast<cd*>(pr.coef),
                                                        d_rhat, pr.k0, pref, rule, static_cast<cd*>(E));
   }
@@ -568,7 +855,7 @@ pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, v
   const double w2e = pr.w * pr.w * eps0();
   if (pr.io_f32()) {
     k_coef<float><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cf*>(x), pr.perm, pr.tri_edge,
-                                                   pr.tri_c, pr.tri_dcp, w2e, static_cast<cf*>(coef));
+                                                   pr.tri_c, pr.tri_dcp, w2e, static_cast<cf*>(coef), nullptr);
     k_near<float, float><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
                                                                pr.near_idx, pr.row_ptr, static_cast<const cf*>(pr.mom),
                                                                static_cast<const cf*>(coef), float(kMu0),
@@ -576,12 +863,14 @@ pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, v
     k_assemble<float><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                        pr.inv_perm, static_cast<const cf*>(pot), static_cast<cf*>(y));
   } else {
+    const bool split = pr.near_f32();
     k_coef<double><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cd*>(x), pr.perm, pr.tri_edge,
-                                                    pr.tri_c, pr.tri_dcp, w2e, static_cast<cd*>(coef));
-    if (pr.near_f32())
+                                                    pr.tri_c, pr.tri_dcp, w2e, split ? nullptr : static_cast<cd*>(coef),
+                                                    split ? static_cast<cf*>(coef) : nullptr);
+    if (split)
       k_near<float, double><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
           pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.row_ptr,
-          static_cast<const cf*>(pr.mom), static_cast<const cd*>(coef), float(kMu0), static_cast<cd*>(pot));
+          static_cast<const cf*>(pr.mom), static_cast<const cf*>(coef), float(kMu0), static_cast<cd*>(pot));
     else
       k_near<double, double><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
           pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.row_ptr,

@@ -77,6 +77,7 @@ struct Problem {
   void* M = nullptr;             // [T][3][P]
   void* F = nullptr;             // [P][P]  F[p][p'] (far precision, real)
   void* Ft = nullptr;            // [P][P]  F[p'][p]
+  void* Kf = nullptr;            // [2 ntheta][ntheta][ntheta] azimuthal blocks of F (real)
   std::vector<LevelDev> lev;     // [L+1]
 
   // per-stage CUDA-event profiling (pie_profile_begin / pie_profile_end)
@@ -85,6 +86,7 @@ struct Problem {
 
   // work buffers
   void* coef = nullptr;          // [T][6] complex (io precision)
+  void* coef32 = nullptr;        // [T][6] complex float copy for the MIXED near part
   void* pot = nullptr;           // [T][6]
 
   bool near_f32() const { return par.precision != PIE_FP64; }

@@ -228,6 +228,8 @@ __global__ void __launch_bounds__(128) k_near_build(int64_t T, int64_t nnz, cons
 
 // Leaf radiation tables at kappa_L: Pi_t(p) = int_t exp(-i kappa khat_p.(r - C_b)),
 // M_t(p) = int_t (r - c_t) exp(-i kappa khat_p.(r - C_b)); 7-point rule.
+// Called with P = the half grid (theta rows 0..ntheta/2-1): the other half
+// is the complex conjugate.
 template <typename Rf>
 __global__ void k_rad(int64_t T, int P, const double* __restrict__ vert, const double* __restrict__ cent,
                       const double* __restrict__ area, const int32_t* __restrict__ leaf_of,
@@ -352,6 +354,23 @@ __global__ void k_filter(int P, int ntheta, double ratio, const double* __restri
   double v = sum * wgt[q];
   F[(int64_t)p * P + q] = Rf(v);
   Ft[(int64_t)q * P + p] = Rf(v);
+}
+
+// Azimuthal blocks of the block-circulant filter:
+// K_m[i][k] = (1/NPHI) sum_d F[(i, d)][(k, 0)] cos(2 pi m d / NPHI)
+// (F[(i,d)][(k,0)] is even in d, so the sine part vanishes).
+template <typename Rf>
+__global__ void k_filter_fourier(int ntheta, const Rf* __restrict__ F, Rf* __restrict__ Kf) {
+  const int nphi = 2 * ntheta, P = ntheta * nphi;
+  int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= nphi * ntheta * ntheta) return;
+  int m = id / (ntheta * ntheta), i = (id / ntheta) % ntheta, k = id % ntheta;
+  double acc = 0;
+  for (int d = 0; d < nphi; ++d) {
+    double c = cospi(2.0 * double(m * d % nphi) / nphi);
+    acc += double(F[(int64_t)(i * nphi + d) * P + k * nphi]) * c;
+  }
+  Kf[id] = Rf(acc / nphi);
 }
 
 // Interpolation phases for the children of level-l boxes:
@@ -489,15 +508,20 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   const int nt = pr.par.ntheta;
   std::vector<double> gx, gw;
   gauss_legendre(nt, gx, gw);
+  // The lower theta rows are computed; the upper rows are their exact
+  // negatives (antipodes), so that -khat is on the grid bit for bit.
   std::vector<double> khat(3 * P), wgt(P);
-  for (int i = 0; i < nt; ++i)
+  for (int i = 0; i < nt / 2; ++i)
     for (int j = 0; j < 2 * nt; ++j) {
       int p = i * 2 * nt + j;
+      int pa = (nt - 1 - i) * 2 * nt + (j + nt) % (2 * nt);
       double ct = gx[i], stt = std::sqrt(1.0 - ct * ct), ph = kPi * j / nt;
       khat[3 * p] = stt * std::cos(ph);
       khat[3 * p + 1] = stt * std::sin(ph);
       khat[3 * p + 2] = ct;
+      for (int d = 0; d < 3; ++d) khat[3 * pa + d] = -khat[3 * p + d];
       wgt[p] = gw[i] * kPi / nt;
+      wgt[pa] = gw[nt - 1 - i] * kPi / nt;
     }
   // 7-point degree-5 rule (Radon), closed form; and the 8 x 8 collapsed Gauss rule
   std::vector<double> r7, r64;
@@ -554,10 +578,10 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
 
   // leaf radiation tables
   const double x = pr.par.kappa_a;
-  pr.Pi = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * P, s);
-  pr.M = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * 3 * P, s);
+  pr.Pi = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * (P / 2), s);
+  pr.M = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * 3 * (P / 2), s);
   if (s != PIE_OK) return s;
-  k_rad<Rf><<<unsigned((T * P + 255) / 256), 256, 0, st>>>(T, P, pr.vert, pr.cent, pr.area, pr.leaf_of,
+  k_rad<Rf><<<unsigned((T * (P / 2) + 255) / 256), 256, 0, st>>>(T, P / 2, pr.vert, pr.cent, pr.area, pr.leaf_of,
                                                            pr.leaf_center, pr.khat, x / aL, pr.rule7,
                                                            static_cast<C2<Rf>*>(pr.Pi), static_cast<C2<Rf>*>(pr.M));
   if ((s = cuda_check(cudaGetLastError(), "radiation tables")) != PIE_OK) return s;
@@ -608,9 +632,14 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   if (s != PIE_OK) return s;
   k_filter<Rf><<<unsigned((P * P + 127) / 128), 128, 0, st>>>(P, nt, 0.5, pr.khat, pr.wgt, static_cast<Rf*>(pr.F),
                                                               static_cast<Rf*>(pr.Ft));
+  pr.Kf = zalloc(pr, sizeof(Rf) * 2 * nt * nt * nt, s);
+  if (s != PIE_OK) return s;
+  k_filter_fourier<Rf><<<unsigned((2 * nt * nt * nt + 127) / 128), 128, 0, st>>>(nt, static_cast<const Rf*>(pr.F),
+                                                                                 static_cast<Rf*>(pr.Kf));
   const size_t cio = pr.io_f32() ? sizeof(cf) : sizeof(cd);
   pr.coef = zalloc(pr, cio * 6 * size_t(T), s);
   pr.pot = zalloc(pr, cio * 6 * size_t(T), s);
+  if (pr.par.precision == PIE_MIXED) pr.coef32 = zalloc(pr, sizeof(cf) * 6 * size_t(T), s);
   if (s != PIE_OK) return s;
   if ((s = cuda_check(cudaGetLastError(), "setup launch")) != PIE_OK) return s;
   return cuda_check(cudaStreamSynchronize(st), "setup");

@@ -87,7 +87,8 @@ def test_fp64_stages_match_oracle_mlfma(pg, mesh3, oracle3, L):
     om = [m0, mt[:, 0], mt[:, 1], mt[:, 2], ms[:, 0], ms[:, 1], ms[:, 2], mts]
     for k in range(8):
         assert np.max(np.abs(mom[k] - om[k])) <= 1e-12 * np.max(np.abs(om[k])), k
-    assert rel(pr.stage(5), M.Pi) < 1e-12 and rel(pr.stage(6), M.M) < 1e-12
+    half = pr.P // 2
+    assert rel(pr.stage(5), M.Pi[:, :half]) < 1e-12 and rel(pr.stage(6), M.M[:, :, :half]) < 1e-12
     yno = M.assemble(M.near_potentials(st["coef"]))
     assert rel(yn, yno) < 1e-12
     for l in range(3, L + 1):
