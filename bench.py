@@ -3,7 +3,7 @@
 Workload: PEC sphere R = 1 m, icosahedral mesh subdivided 7 times
 (327,680 triangles, 491,520 RWG functions, N = 819,200 unknowns -- the
 "1M unknowns" point), kR = 1e-3, 7-level MLFMA (leaf box 1/32 m),
-tau = 7, kappa a = 0.06, N_theta = 8 (P = 128).  One step = one product
+tau = 7, kappa a = 0.08, N_theta = 8 (P = 128).  One step = one product
 y = Z x (all stages: coefficients, near part, aggregation, interpolation,
 translations at levels 3..7, anterpolation, disaggregation, assembly) on a
 complex-normal x (seed 1234) resident in HBM.  The headline `value` is the
@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(workload="pec_sphere_icosphere7_1M", mesh="icosphere n=7, R=1 m", triangles=327680,
-                rwg=491520, N=819200, kR=1e-3, levels=7, leaf_m=1.0 / 32, tau=7, kappa_a=0.06, ntheta=8, P=128,
+                rwg=491520, N=819200, kR=1e-3, levels=7, leaf_m=1.0 / 32, tau=7, kappa_a=0.08, ntheta=8, P=128,
                 nrhs=1)
 METRIC = "PIE MLFMA matvecs/s (1M unk)"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rows", type=int, default=4, help="rows of the dense oracle product for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES time-to-tolerance measurement")
+    ap.add_argument("--gmres-tol", type=float, default=1e-6)
     ap.add_argument("--mesh-level", type=int, default=7,
                     help="icosphere subdivision n (L = n levels); 7 is the timed workload, smaller for profiling")
     return ap.parse_args()
@@ -204,11 +206,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+        gm = None
+        if not args.no_gmres:
+            gm = gmres_run(pr, args.gmres_tol, k0, barrier, max_over_ranks)
         launches_per = 1 + 1 + 1 + (pr.L - 3) + (pr.L - 2) + (pr.L - 3) + 1 + 1
         results[mode] = dict(pr=pr, ms=ms_max, stage_ms=stage_ms, napplies=napplies, clocks=clk.summary(),
                              e2e_ms=e2e_ms, setup_s=setup_s, launches=launches_per * args.steps,
                              bytes_io=x.numel() * x.element_size(), device_bytes=pr.device_bytes,
-                             near_pairs=pr.near_pairs)
+                             near_pairs=pr.near_pairs, gmres=gm)
         del x, y, xd, yd
     if world > 1:
         dist.destroy_process_group()
@@ -256,7 +261,9 @@ def run_ours(args):
         "stage_share": stage_share,
         "fp64": {"value": world * K / (fp["ms"] * 1e-3), "ms_per_step": fp["ms"] / K,
                  "stage_ms_per_step": {k: v / K for k, v in fp["stage_ms"].items()},
-                 "e2e_value": world * K / (fp["e2e_ms"] * 1e-3), "setup_s": fp["setup_s"]},
+                 "e2e_value": world * K / (fp["e2e_ms"] * 1e-3), "setup_s": fp["setup_s"],
+                 "gmres": fp["gmres"]},
+        "gmres": main["gmres"],
         "setup_s": main["setup_s"],
         "device_bytes": main["device_bytes"],
         "clocks": main["clocks"],
@@ -264,6 +271,36 @@ def run_ours(args):
     if not args.no_cpu_baseline and nlev == 7:
         line["cpu_baseline"] = cpu_baseline(args.cpu_rows)
     print(json.dumps(line))
+
+
+def rayleigh_eplane(k0, R, cosg):
+    """Bistatic E-plane RCS of a small PEC sphere (Rayleigh limit, relative
+    error O((kR)^2)): 4 pi R^2 (kR)^4 (cos g - 1/2)^2."""
+    return 4 * 3.141592653589793 * R * R * (k0 * R) ** 4 * (cosg - 0.5) ** 2
+
+
+def gmres_run(pr, tol, k0, barrier, max_over_ranks):
+    """GMRES(100) time to ||b - Z x|| <= tol ||b|| for the plane wave along -z,
+    x-polarised, and the E-plane RCS of the solution against the Rayleigh
+    limit (exact to ~(kR)^2 = 1e-6 at kR = 1e-3)."""
+    import numpy as np
+    import torch
+
+    import pie_inputs as pi
+    b = pr.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
+    torch.cuda.synchronize()
+    barrier()
+    x, st = pr.solve(b, tol=tol, maxit=3000, restart=100)
+    barrier()
+    rh = pi.bistatic_directions(181)
+    E = pr.farfield(x, rh).cpu().numpy()
+    s = 4 * np.pi * np.sum(np.abs(E) ** 2, axis=1)
+    sm = rayleigh_eplane(k0, 1.0, -rh[:, 2])
+    mask = sm > 1e-2 * sm.max()
+    return {"tol": tol, "iterations": st["iterations"], "seconds": max_over_ranks(st["seconds"]),
+            "rel_residual": st["rel_residual"], "converged": st["converged"], "restart": 100,
+            "rcs_max_db_err_vs_rayleigh": float(np.max(np.abs(10 * np.log10(s[mask] / sm[mask])))),
+            "rcs_db": [float(v) for v in 10 * np.log10(s[::30])]}
 
 
 CPU_SNIPPET = r"""

@@ -102,8 +102,10 @@ typedef struct {
 /* Message of the last failed call on this thread ("" if none). */
 const char* pie_last_error(void);
 
-/* Default parameters: levels 3, root_side 0, tau 7, kappa_a 0.06, ntheta 8,
- * precision PIE_FP64 (the values of the error search of Eqs. (4)-(5)). */
+/* Default parameters: levels 3, root_side 0, tau 7, kappa_a 0.08, ntheta 8,
+ * precision PIE_FP64: product error below 1e-3 with an FP64 rounding
+ * nonlinearity (~2.5e-6) low enough for GMRES to reach 1e-6 (the error and
+ * rounding trade-off of Eqs. (4)-(5)). */
 void pie_params_default(pie_params* p);
 
 /* Surface mesh (Section 2: triangulated surface S).  xyz: nv x 3 doubles

@@ -57,7 +57,7 @@ def interpolation_filter(khat, w, ntheta, ratio):
 
 
 class MLFMA:
-    def __init__(self, xyz, tri, k0, L, tau=7, x=0.06, ntheta=8, side=0.0):
+    def __init__(self, xyz, tri, k0, L, tau=7, x=0.08, ntheta=8, side=0.0):
         self.top = build_topology(xyz, tri)
         self.geo = Geometry(xyz, tri)
         self.k0 = float(k0)

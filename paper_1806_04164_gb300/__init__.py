@@ -22,7 +22,7 @@ STATUS = {0: "PIE_OK", 1: "PIE_ERR_PARAM", 2: "PIE_ERR_NONMANIFOLD", 3: "PIE_ERR
           8: "PIE_ERR_NOCONV", 9: "PIE_ERR_BREAKDOWN", 10: "PIE_ERR_NAN"}
 
 # Parameters found by the Eq. (4)-(5) error search (truncation tau, kappa*a, N_theta).
-DEFAULT_TAU, DEFAULT_KAPPA_A, DEFAULT_NTHETA = 7, 0.06, 8
+DEFAULT_TAU, DEFAULT_KAPPA_A, DEFAULT_NTHETA = 7, 0.08, 8
 
 
 class PieError(RuntimeError):

@@ -30,7 +30,7 @@ void pie_params_default(pie_params* p) {
   p->levels = 3;
   p->root_side = 0.0;
   p->tau = 7;
-  p->kappa_a = 0.06;
+  p->kappa_a = 0.08;
   p->ntheta = 8;
   p->precision = PIE_FP64;
 }

@@ -457,23 +457,25 @@ __global__ void k_anterp(int P, const int32_t* __restrict__ parent, const int8_t
   }
 }
 
-// a6: leaf disaggregation with the receiving (conjugate) patterns; one warp
-// per triangle, lanes over half-grid samples.  Over a sample pair (q, -q):
+// a6: leaf disaggregation with the receiving (conjugate) patterns.  One
+// thread per triangle; the receiving tables are stored sample-major
+// ([Ph][T], [3][Ph][T]) so that consecutive threads read consecutive
+// triangles, and the incoming pattern of the leaf box is shared through the
+// cache.  Over a sample pair (q, -q):
 // conj(X(q)) G(q) + X(q) G(-q) = Xr (G(q) + G(-q)) - i Xi (G(q) - G(-q)).
 // Adds to pot[t].
 template <typename Rf, typename Rio>
 __global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, int ntheta, const int32_t* __restrict__ leaf_of,
-                                                const C2<Rf>* __restrict__ Pi, const C2<Rf>* __restrict__ M,
+                                                const C2<Rf>* __restrict__ PiR, const C2<Rf>* __restrict__ MR,
                                                 const C2<Rf>* __restrict__ G, C2<Rio>* __restrict__ pot) {
-  int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= T) return;
   const int Ph = P / 2;
   const C2<Rf>* g = G + (int64_t)leaf_of[t] * kComp * P;
   C2<Rf> acc[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) acc[i] = mk<Rf>(0, 0);
-  for (int q = lane; q < Ph; q += 32) {
+  for (int q = 0; q < Ph; ++q) {
     const int qa = antipode(q, ntheta);
     C2<Rf> gs[kComp], gd[kComp];
 #pragma unroll
@@ -482,10 +484,10 @@ __global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, int ntheta, co
       gs[c] = mk<Rf>(u.x + v.x, u.y + v.y);
       gd[c] = mk<Rf>(u.x - v.x, u.y - v.y);
     }
-    C2<Rf> pi = Pi[t * Ph + q];
+    C2<Rf> pi = PiR[(int64_t)q * T + t];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      C2<Rf> m = M[(t * 3 + d) * Ph + q];
+      C2<Rf> m = MR[((int64_t)d * Ph + q) * T + t];
       // U += Mr gs - i Mi gd
       rfma(acc[0], m.x, gs[d]);
       acc[0].x = fma(m.y, gd[d].y, acc[0].x);
@@ -502,18 +504,11 @@ __global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, int ntheta, co
       acc[1 + c].y = fma(-pi.y, gd[c].x, acc[1 + c].y);
     }
   }
+  C2<Rio>* o = pot + 6 * t;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    acc[i].x = warp_sum(acc[i].x);
-    acc[i].y = warp_sum(acc[i].y);
-  }
-  if (lane == 0) {
-    C2<Rio>* o = pot + 6 * t;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      o[i].x = Rio(double(o[i].x) + double(acc[i].x));
-      o[i].y = Rio(double(o[i].y) + double(acc[i].y));
-    }
+    o[i].x = Rio(double(o[i].x) + double(acc[i].x));
+    o[i].y = Rio(double(o[i].y) + double(acc[i].y));
   }
 }
 
@@ -648,8 +643,9 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st
   }
   prof_mark(pr, 5, true, st);
   prof_mark(pr, 6, false, st);
-  k_disagg<Rf, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, P, pr.par.ntheta, pr.leaf_of, Pi, M,
-                                                         static_cast<const C2<Rf>*>(pr.lev[L].G), pot);
+  k_disagg<Rf, Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, P, pr.par.ntheta, pr.leaf_of,
+                                                    static_cast<const C2<Rf>*>(pr.PiR), static_cast<const C2<Rf>*>(pr.MR),
+                                                    static_cast<const C2<Rf>*>(pr.lev[L].G), pot);
   prof_mark(pr, 6, true, st);
   prof_mark(pr, 7, false, st);
   k_assemble<Rio><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,

@@ -73,8 +73,10 @@ struct Problem {
 
   // operator tables
   void* mom = nullptr;           // [8][nnz] complex (near precision)
-  void* Pi = nullptr;            // [T][P]
-  void* M = nullptr;             // [T][3][P]
+  void* Pi = nullptr;            // [T][P/2]
+  void* M = nullptr;             // [T][3][P/2] radiation tables (half grid), triangle-major
+  void* PiR = nullptr;           // [P/2][T]    the same tables, sample-major (receiving side)
+  void* MR = nullptr;            // [3][P/2][T]
   void* F = nullptr;             // [P][P]  F[p][p'] (far precision, real)
   void* Ft = nullptr;            // [P][P]  F[p'][p]
   void* Kf = nullptr;            // [2 ntheta][ntheta][ntheta] azimuthal blocks of F (real)

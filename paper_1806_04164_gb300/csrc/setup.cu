@@ -234,7 +234,8 @@ template <typename Rf>
 __global__ void k_rad(int64_t T, int P, const double* __restrict__ vert, const double* __restrict__ cent,
                       const double* __restrict__ area, const int32_t* __restrict__ leaf_of,
                       const double* __restrict__ leaf_center, const double* __restrict__ khat, double kappa,
-                      const double* __restrict__ rule7, C2<Rf>* __restrict__ Pi, C2<Rf>* __restrict__ M) {
+                      const double* __restrict__ rule7, C2<Rf>* __restrict__ Pi, C2<Rf>* __restrict__ M,
+                      C2<Rf>* __restrict__ PiR, C2<Rf>* __restrict__ MR) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= T * P) return;
   int64_t t = i / P;
@@ -260,6 +261,8 @@ __global__ void k_rad(int64_t T, int P, const double* __restrict__ vert, const d
   }
   Pi[t * P + p] = mk<Rf>(Rf(pr), Rf(pi));
   for (int d = 0; d < 3; ++d) M[(t * 3 + d) * P + p] = mk<Rf>(Rf(mr[d]), Rf(mi[d]));
+  PiR[(int64_t)p * T + t] = mk<Rf>(Rf(pr), Rf(pi));
+  for (int d = 0; d < 3; ++d) MR[((int64_t)d * P + p) * T + t] = mk<Rf>(Rf(mr[d]), Rf(mi[d]));
 }
 
 // Translation operator of Eq. (5) with the quadrature weight and the
@@ -580,10 +583,13 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   const double x = pr.par.kappa_a;
   pr.Pi = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * (P / 2), s);
   pr.M = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * 3 * (P / 2), s);
+  pr.PiR = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * (P / 2), s);
+  pr.MR = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * 3 * (P / 2), s);
   if (s != PIE_OK) return s;
   k_rad<Rf><<<unsigned((T * (P / 2) + 255) / 256), 256, 0, st>>>(T, P / 2, pr.vert, pr.cent, pr.area, pr.leaf_of,
                                                            pr.leaf_center, pr.khat, x / aL, pr.rule7,
-                                                           static_cast<C2<Rf>*>(pr.Pi), static_cast<C2<Rf>*>(pr.M));
+                                                           static_cast<C2<Rf>*>(pr.Pi), static_cast<C2<Rf>*>(pr.M),
+                                                           static_cast<C2<Rf>*>(pr.PiR), static_cast<C2<Rf>*>(pr.MR));
   if ((s = cuda_check(cudaGetLastError(), "radiation tables")) != PIE_OK) return s;
 
   // levels

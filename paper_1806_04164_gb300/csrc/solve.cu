@@ -1,11 +1,353 @@
-// GMRES on the PIE system (Section 4).
-#include "problem.h"
+// Restarted GMRES on the PIE system (Section 4 solves with GMRES).
+//
+// The system is scaled symmetrically, A = D Z D with D = |diag Z|^{-1/2}
+// (the diagonal comes from the near-part self and neighbour pair moments), so
+// that the RWG and pulse blocks, whose physical units differ, are balanced.
+// Arnoldi runs on the device in complex double with classical Gram-Schmidt
+// applied twice; dot products use fixed-order two-pass reductions (results do
+// not depend on scheduling).  The small Hessenberg problem (Givens rotations)
+// is solved on the host.  Stopping test: ||b - Z x|| / ||b|| <= tol on the
+// unscaled system, recomputed from the true residual at every restart.
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "device.cuh"
 
 namespace pie {
 
-pie_status solve(Problem&, const void*, void*, double, int, int, pie_solve_stats*, cudaStream_t) {
-  set_error("pie_solve: not built in this version");
-  return PIE_ERR_PARAM;
+typedef std::complex<double> zc;
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs
+constexpr int kRedThreads = 256;
+
+static inline unsigned nb_(int64_t n, int b) { return unsigned((n + b - 1) / b); }
+
+// Entry index of the pair (test t, source s) in the near moment planes, or -1.
+__device__ int64_t near_entry(int64_t t, int64_t s, const int32_t* leaf_of, const int32_t* leaf_start,
+                              const int32_t* near_ptr, const int32_t* near_idx, const int64_t* row_ptr) {
+  int bt = leaf_of[t], bs = leaf_of[s];
+  int64_t e = row_ptr[t];
+  for (int qi = near_ptr[bt]; qi < near_ptr[bt + 1]; ++qi) {
+    int q = near_idx[qi];
+    if (q == bs) return e + (s - leaf_start[q]);
+    e += leaf_start[q + 1] - leaf_start[q];
+  }
+  return -1;
+}
+
+// |Z_ii|^{-1/2} for every unknown (mesh order), from the near pair moments.
+template <typename Rm>
+__global__ void k_diag_scale(int64_t N, int64_t E, int64_t nnz, const int32_t* __restrict__ edge_tt,
+                             const int8_t* __restrict__ edge_k, const double* __restrict__ tri_c,
+                             const double* __restrict__ tri_dcp, const int64_t* __restrict__ inv_perm,
+                             const int32_t* __restrict__ leaf_of, const int32_t* __restrict__ leaf_start,
+                             const int32_t* __restrict__ near_ptr, const int32_t* __restrict__ near_idx,
+                             const int64_t* __restrict__ row_ptr, const C2<Rm>* __restrict__ mom, double w2e,
+                             double* __restrict__ dscale) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double zr = 0, zi = 0;
+  if (i < E) {
+    for (int s1 = 0; s1 < 2; ++s1)
+      for (int s2 = 0; s2 < 2; ++s2) {
+        int64_t t1 = edge_tt[2 * i + s1], t2 = edge_tt[2 * i + s2];
+        int k1 = edge_k[2 * i + s1], k2 = edge_k[2 * i + s2];
+        int64_t e = near_entry(t1, t2, leaf_of, leaf_start, near_ptr, near_idx, row_ptr);
+        if (e < 0) continue;
+        const double* d1 = tri_dcp + 9 * t1 + 3 * k1;
+        const double* d2 = tri_dcp + 9 * t2 + 3 * k2;
+        double cc = kMu0 * tri_c[3 * t1 + k1] * tri_c[3 * t2 + k2];
+        C2<Rm> m0 = mom[e], mts = mom[7 * nnz + e];
+        double vr = double(mts.x), vi = double(mts.y), dd = 0;
+        for (int d = 0; d < 3; ++d) {
+          C2<Rm> mt = mom[(1 + d) * nnz + e], ms = mom[(4 + d) * nnz + e];
+          vr += d1[d] * double(ms.x) + double(mt.x) * d2[d];
+          vi += d1[d] * double(ms.y) + double(mt.y) * d2[d];
+          dd += d1[d] * d2[d];
+        }
+        vr += dd * double(m0.x);
+        vi += dd * double(m0.y);
+        zr += cc * vr;
+        zi += cc * vi;
+      }
+  } else {
+    int64_t t = inv_perm[i - E];
+    int64_t e = near_entry(t, t, leaf_of, leaf_start, near_ptr, near_idx, row_ptr);
+    C2<Rm> m0 = mom[e];
+    zr = w2e * double(m0.x);
+    zi = w2e * double(m0.y);
+  }
+  double a = sqrt(zr * zr + zi * zi);
+  dscale[i] = a > 0 ? 1.0 / sqrt(a) : 1.0;
+}
+
+__global__ void k_scale(int64_t N, const double* __restrict__ d, const cd* __restrict__ x, cd* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) y[i] = mk<double>(d[i] * x[i].x, d[i] * x[i].y);
+}
+
+// y = a - b (elementwise)
+__global__ void k_sub(int64_t N, const cd* __restrict__ a, const cd* __restrict__ b, cd* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) y[i] = mk<double>(a[i].x - b[i].x, a[i].y - b[i].y);
+}
+
+// y = alpha x
+__global__ void k_axs(int64_t N, double ar, double ai, const cd* __restrict__ x, cd* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) y[i] = mk<double>(ar * x[i].x - ai * x[i].y, ar * x[i].y + ai * x[i].x);
+}
+
+// partial[v][blk] = sum_{n in blk's slice} conj(V[v][n]) w[n], v < nv.
+// Pass 1 of a fixed-order reduction.
+__global__ void __launch_bounds__(kRedThreads) k_mdot(int64_t N, int nv, const cd* __restrict__ V, int64_t ldv,
+                                                      const cd* __restrict__ w, cd* __restrict__ partial) {
+  __shared__ double sr[kRedThreads / 32], si[kRedThreads / 32];
+  const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+  const int64_t n0 = blockIdx.x * per, n1 = min(N, n0 + per);
+  for (int v = 0; v < nv; ++v) {
+    const cd* vv = V + v * ldv;
+    double ar = 0, ai = 0;
+    for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+      cd a = vv[n], b = w[n];
+      ar += a.x * b.x + a.y * b.y;
+      ai += a.x * b.y - a.y * b.x;
+    }
+    ar = warp_sum(ar);
+    ai = warp_sum(ai);
+    if ((threadIdx.x & 31) == 0) {
+      sr[threadIdx.x >> 5] = ar;
+      si[threadIdx.x >> 5] = ai;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tr = 0, ti = 0;
+      for (int k = 0; k < kRedThreads / 32; ++k) {
+        tr += sr[k];
+        ti += si[k];
+      }
+      partial[(int64_t)v * gridDim.x + blockIdx.x] = mk<double>(tr, ti);
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 2: out[v] = sum over blocks of partial[v][.], in block order.
+__global__ void k_mdot_finish(int nv, int nblk, const cd* __restrict__ partial, cd* __restrict__ out) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  double r = 0, i = 0;
+  for (int b = 0; b < nblk; ++b) {
+    r += partial[(int64_t)v * nblk + b].x;
+    i += partial[(int64_t)v * nblk + b].y;
+  }
+  out[v] = mk<double>(r, i);
+}
+
+// w -= sum_v h[v] V[v]   (or w += when sign = +1)
+__global__ void k_mupdate(int64_t N, int nv, const cd* __restrict__ V, int64_t ldv, const cd* __restrict__ h,
+                          double sign, cd* __restrict__ w) {
+  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double r = w[n].x, i = w[n].y;
+  for (int v = 0; v < nv; ++v) {
+    cd a = V[v * ldv + n], c = h[v];
+    r += sign * (c.x * a.x - c.y * a.y);
+    i += sign * (c.x * a.y + c.y * a.x);
+  }
+  w[n] = mk<double>(r, i);
+}
+
+// ---------------------------------------------------------------- host loop
+
+struct Work {
+  std::vector<void*> ptrs;
+  ~Work() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  T* get(size_t n, pie_status& s) {
+    if (s != PIE_OK) return nullptr;
+    void* p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pie_solve: device allocation failed");
+      s = PIE_ERR_OOM;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+};
+
+// conj(a) . b over N entries, deterministic.
+static pie_status dotc(int64_t N, int nv, const cd* V, int64_t ldv, const cd* w, cd* partial, cd* out_dev,
+                       zc* out_host, cudaStream_t st) {
+  k_mdot<<<kRedBlocks, kRedThreads, 0, st>>>(N, nv, V, ldv, w, partial);
+  k_mdot_finish<<<nb_(nv, 128), 128, 0, st>>>(nv, kRedBlocks, partial, out_dev);
+  pie_status s = cuda_check(cudaMemcpyAsync(out_host, out_dev, sizeof(cd) * nv, cudaMemcpyDeviceToHost, st), "dot");
+  if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(st), "dot sync");
+  return s;
+}
+
+pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, int restart, pie_solve_stats* stats,
+                 cudaStream_t st) {
+  if (pr.io_f32()) {
+    set_error("pie_solve: needs a PIE_FP64 or PIE_MIXED problem (complex double vectors)");
+    return PIE_ERR_PARAM;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t N = pr.N;
+  const int m = std::min(restart, maxit);
+  pie_status s = PIE_OK;
+  Work wk;
+  double* d = wk.get<double>(N, s);
+  cd* V = wk.get<cd>(size_t(N) * (m + 1), s);
+  cd* w = wk.get<cd>(N, s);
+  cd* u = wk.get<cd>(N, s);
+  cd* r = wk.get<cd>(N, s);
+  cd* partial = wk.get<cd>(size_t(kRedBlocks) * (m + 1), s);
+  cd* hdev = wk.get<cd>(m + 1, s);
+  if (s != PIE_OK) return s;
+  const cd* b = static_cast<const cd*>(bv);
+  cd* x = static_cast<cd*>(xv);
+  const double w2e = pr.w * pr.w * eps0();
+  if (pr.near_f32())
+    k_diag_scale<float><<<nb_(N, 256), 256, 0, st>>>(N, pr.E, pr.nnz, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                     pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx,
+                                                     pr.row_ptr, static_cast<const cf*>(pr.mom), w2e, d);
+  else
+    k_diag_scale<double><<<nb_(N, 256), 256, 0, st>>>(N, pr.E, pr.nnz, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                      pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
+                                                      pr.near_idx, pr.row_ptr, static_cast<const cd*>(pr.mom), w2e, d);
+  cudaMemsetAsync(x, 0, sizeof(cd) * N, st);
+  cudaMemcpyAsync(r, b, sizeof(cd) * N, cudaMemcpyDeviceToDevice, st);
+  zc tmp[1];
+  if ((s = dotc(N, 1, b, N, b, partial, hdev, tmp, st)) != PIE_OK) return s;
+  const double bn = std::sqrt(tmp[0].real());
+  int it = 0;
+  double rel = 1.0;
+  pie_status result = PIE_ERR_NOCONV;
+  std::vector<zc> H(size_t(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), h2(m + 1);
+  if (bn == 0) {
+    result = PIE_OK;
+    rel = 0;
+  }
+  while (result != PIE_OK && it < maxit) {
+    if ((s = dotc(N, 1, r, N, r, partial, hdev, tmp, st)) != PIE_OK) return s;
+    rel = std::sqrt(tmp[0].real()) / bn;
+    if (!std::isfinite(rel)) {
+      set_error("pie_solve: non-finite residual");
+      return PIE_ERR_NAN;
+    }
+    if (rel <= tol) {
+      result = PIE_OK;
+      break;
+    }
+    // scaled residual D r as the first Krylov vector
+    k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, r, V);
+    if ((s = dotc(N, 1, V, N, V, partial, hdev, tmp, st)) != PIE_OK) return s;
+    double beta = std::sqrt(tmp[0].real());
+    k_axs<<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / beta, 0.0, V, V);
+    std::fill(H.begin(), H.end(), zc(0));
+    std::fill(g.begin(), g.end(), zc(0));
+    g[0] = beta;
+    int j = 0;
+    bool breakdown = false;
+    const double dbn = beta / rel;  // ~ ||D b|| scale for the inner estimate
+    for (; j < m && it < maxit; ++j) {
+      cd* vj = V + size_t(j) * N;
+      k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, vj, u);
+      if ((s = apply_one(pr, u, w, st)) != PIE_OK) return s;
+      k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, w, w);
+      // classical Gram-Schmidt, twice
+      if ((s = dotc(N, j + 1, V, N, w, partial, hdev, h.data(), st)) != PIE_OK) return s;
+      k_mupdate<<<nb_(N, 256), 256, 0, st>>>(N, j + 1, V, N, hdev, -1.0, w);
+      if ((s = dotc(N, j + 1, V, N, w, partial, hdev, h2.data(), st)) != PIE_OK) return s;
+      k_mupdate<<<nb_(N, 256), 256, 0, st>>>(N, j + 1, V, N, hdev, -1.0, w);
+      for (int i = 0; i <= j; ++i) h[i] += h2[i];
+      if ((s = dotc(N, 1, w, N, w, partial, hdev, tmp, st)) != PIE_OK) return s;
+      double hn = std::sqrt(tmp[0].real());
+      for (int i = 0; i <= j; ++i)
+        if (!std::isfinite(h[i].real()) || !std::isfinite(h[i].imag())) {
+          set_error("pie_solve: non-finite Arnoldi coefficient");
+          return PIE_ERR_NAN;
+        }
+      for (int i = 0; i <= j; ++i) H[size_t(i) * m + j] = h[i];
+      H[size_t(j + 1) * m + j] = hn;
+      // previous rotations, then a new one: G = [[conj c, conj s], [-s, c]]
+      for (int i = 0; i < j; ++i) {
+        zc a = H[size_t(i) * m + j], c2 = H[size_t(i + 1) * m + j];
+        H[size_t(i) * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * c2;
+        H[size_t(i + 1) * m + j] = -sn[i] * a + cs[i] * c2;
+      }
+      zc a = H[size_t(j) * m + j];
+      double den = std::sqrt(std::norm(a) + hn * hn);
+      cs[j] = a / den;
+      sn[j] = zc(hn / den);
+      H[size_t(j) * m + j] = den;
+      H[size_t(j + 1) * m + j] = 0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = std::conj(cs[j]) * g[j];
+      ++it;
+      if (hn <= 1e-14 * den) {
+        breakdown = true;
+        ++j;
+        break;
+      }
+      k_axs<<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / hn, 0.0, w, V + size_t(j + 1) * N);
+      if (std::abs(g[j + 1]) <= 0.5 * tol * dbn) {
+        ++j;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular), x += D V y
+    std::vector<zc> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      zc acc = g[i];
+      for (int k = i + 1; k < j; ++k) acc -= H[size_t(i) * m + k] * y[k];
+      y[i] = acc / H[size_t(i) * m + i];
+    }
+    std::vector<cd> yh(j);
+    for (int i = 0; i < j; ++i) yh[i] = cd{y[i].real(), y[i].imag()};
+    cudaMemcpyAsync(hdev, yh.data(), sizeof(cd) * j, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(u, 0, sizeof(cd) * N, st);
+    k_mupdate<<<nb_(N, 256), 256, 0, st>>>(N, j, V, N, hdev, 1.0, u);
+    k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, u, u);
+    {
+      // x += u
+      cd one = {1.0, 0.0};
+      cudaMemcpyAsync(hdev, &one, sizeof(cd), cudaMemcpyHostToDevice, st);
+      k_mupdate<<<nb_(N, 256), 256, 0, st>>>(N, 1, u, N, hdev, 1.0, x);
+    }
+    // true residual r = b - Z x
+    if ((s = apply_one(pr, x, w, st)) != PIE_OK) return s;
+    k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, w, r);
+    if ((s = cuda_check(cudaGetLastError(), "gmres launch")) != PIE_OK) return s;
+    if (breakdown) {
+      if ((s = dotc(N, 1, r, N, r, partial, hdev, tmp, st)) != PIE_OK) return s;
+      rel = std::sqrt(tmp[0].real()) / bn;
+      result = rel <= tol ? PIE_OK : PIE_ERR_BREAKDOWN;
+      if (result != PIE_OK) set_error("pie_solve: Arnoldi breakdown before convergence");
+      break;
+    }
+  }
+  if (result != PIE_OK && result != PIE_ERR_BREAKDOWN) {
+    if ((s = dotc(N, 1, r, N, r, partial, hdev, tmp, st)) != PIE_OK) return s;
+    rel = std::sqrt(tmp[0].real()) / bn;
+    if (rel <= tol)
+      result = PIE_OK;
+    else
+      set_error("pie_solve: tolerance not reached in maxit iterations");
+  }
+  if ((s = cuda_check(cudaStreamSynchronize(st), "gmres sync")) != PIE_OK) return s;
+  if (stats) {
+    stats->iterations = it;
+    stats->rel_residual = rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return result;
 }
 
 }  // namespace pie

@@ -1,0 +1,68 @@
+"""GMRES on the GPU (Section 4) and the far field of its solution against the
+Mie series: the 1280-triangle PEC sphere, R = 1 m, kR = 0.01, x-polarised
+plane wave along -z, 3-level MLFMA (leaf box 0.5 m)."""
+import numpy as np
+import pytest
+
+import pie_inputs as pi
+
+pytestmark = pytest.mark.gpu
+K = 0.01
+
+
+@pytest.fixture(scope="module")
+def pg():
+    from tests._lib import ensure_built
+    ensure_built()
+    import paper_1806_04164_gb300 as pg
+    return pg
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_solve_rcs_matches_mie(pg, prec):
+    from oracle import mie
+    xyz, tri = pi.icosphere(3)
+    pr = pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=2.0, precision=prec)
+    b = pr.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
+    x, st = pr.solve(b, tol=1e-6, maxit=2000, restart=100)
+    assert st["converged"] and st["rel_residual"] <= 1e-6, st
+    import torch
+    r = b - pr.apply(x)
+    # the recomputed residual repeats the operator's rounding (~3e-6 nonlinearity)
+    assert torch.linalg.norm(r).item() <= 5e-6 * torch.linalg.norm(b).item()
+    rh = pi.bistatic_directions(181)
+    s = 4 * np.pi * np.sum(np.abs(pr.farfield(x, rh).cpu().numpy()) ** 2, axis=1)
+    sm = mie.rcs_eplane(K, 1.0, -rh[:, 2])
+    mask = sm > 1e-2 * sm.max()
+    assert np.max(np.abs(10 * np.log10(s[mask] / sm[mask]))) < 0.1
+    print("GMRES iterations", st["iterations"], "seconds", st["seconds"])
+
+
+def test_solve_matches_dense_solution(pg):
+    import torch
+    from oracle.dense import assemble
+    from oracle.excitation import rhs_planewave
+    from oracle.mesh import build_topology
+    xyz, tri = pi.icosphere(2)
+    top = build_topology(xyz, tri)
+    Z = assemble(top, K)
+    bo = rhs_planewave(top, K, [0, 0, -1.0], [1.0, 0, 0])
+    xo = np.linalg.solve(Z, bo)
+    pr = pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=2.0)
+    x, st = pr.solve(torch.from_numpy(bo).cuda(), tol=1e-5, maxit=2000, restart=200)
+    assert st["converged"]
+    x = x.cpu().numpy()
+    E = top.E
+    # the solution inherits the far-part accuracy of the product (~1e-3)
+    assert np.linalg.norm(x[:E] - xo[:E]) <= 1e-2 * np.linalg.norm(xo[:E])
+
+
+def test_solve_rejects_fp32_and_handles_zero_rhs(pg):
+    import torch
+    xyz, tri = pi.icosphere(2)
+    pr = pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=2.0, precision=pg.PIE_FP32)
+    with pytest.raises(pg.PieError):
+        pr.solve(torch.zeros(pr.N, dtype=torch.complex64, device="cuda"))
+    pr = pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=2.0)
+    x, st = pr.solve(torch.zeros(pr.N, dtype=torch.complex128, device="cuda"))
+    assert st["converged"] and st["iterations"] == 0 and torch.count_nonzero(x).item() == 0

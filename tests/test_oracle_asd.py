@@ -35,12 +35,12 @@ def test_s_equal_one_reduces_to_exact_diagonalization():
 
 
 def test_low_frequency_accuracy_of_chosen_parameters():
-    """tau = 7, N_theta = 8, kappa a = 0.06 over one-box-buffer geometries at
+    """tau = 7, N_theta = 8, kappa a = 0.08 over one-box-buffer geometries at
     k a = 6e-5 and 5e-3: RMS relative error below 1e-3."""
     rng = np.random.default_rng(1)
     offs = far_offsets()
     for k, a in ((1e-3, 0.0625), (1e-2, 0.5)):
-        s = k * a / 0.06
+        s = k * a / 0.08
         errs = []
         for i in range(40):
             d = offs[rng.integers(len(offs))]
