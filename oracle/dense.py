@@ -89,11 +89,13 @@ def assemble(top: Topology, k0: float, chunk=200000, pair_mask=None):
     return Z
 
 
-def rows(top: Topology, k0: float, which, x):
+def rows(top: Topology, k0: float, which, x, pair_mask=None):
     """Selected entries of y = Z x computed row by row without storing Z.
 
     ``which`` holds indices into the mesh-order unknown vector.  Used to check
-    sampled outputs of large problems one by one.
+    sampled outputs of large problems one by one.  ``pair_mask(t, s)`` keeps
+    only the source triangles s (array) paired with test triangle t for which
+    it returns True (e.g. the near part alone).
     """
     E, T = top.E, top.T
     w = C.omega_of_k(k0)
@@ -112,6 +114,9 @@ def rows(top: Topology, k0: float, which, x):
         for t, n in tests:
             tarr = np.full(T, t)
             m0, mt, ms, mts = pair_moments(geo, k0, tarr, allsrc)
+            if pair_mask is not None:
+                keep = pair_mask(t, allsrc)
+                m0, mt, ms, mts = m0 * keep, mt * keep[:, None], ms * keep[:, None], mts * keep
             if n is None:   # pulse test
                 acc += np.sum(w * w * C.EPS0 * m0 * xs)
                 for ks in range(3):

@@ -254,6 +254,7 @@ class Problem:
         return E
 
     def solve(self, b, tol=1e-6, maxit=1000, restart=100, stream=None):
+        """Restarted GMRES on Z x = b (pie_solve)."""
         import torch
         x = torch.zeros_like(b)
         st = SolveStats()

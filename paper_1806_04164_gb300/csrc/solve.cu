@@ -181,14 +181,117 @@ struct Work {
   }
 };
 
-// conj(a) . b over N entries, deterministic.
-static pie_status dotc(int64_t N, int nv, const cd* V, int64_t ldv, const cd* w, cd* partial, cd* out_dev,
-                       zc* out_host, cudaStream_t st) {
-  k_mdot<<<kRedBlocks, kRedThreads, 0, st>>>(N, nv, V, ldv, w, partial);
-  k_mdot_finish<<<nb_(nv, 128), 128, 0, st>>>(nv, kRedBlocks, partial, out_dev);
-  pie_status s = cuda_check(cudaMemcpyAsync(out_host, out_dev, sizeof(cd) * nv, cudaMemcpyDeviceToHost, st), "dot");
-  if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(st), "dot sync");
+// Shared scratch of the Krylov loops.
+struct Ctx {
+  Problem& pr;
+  cudaStream_t st;
+  int64_t N;
+  double* d;        // symmetric scaling
+  cd* u;            // operator scratch
+  cd* partial;      // reduction partials
+  cd* hdev;         // small device vector
+};
+
+// conj(a) . b over N entries, deterministic; result on the host.
+static pie_status dotc(Ctx& c, int nv, const cd* V, const cd* w, zc* out_host) {
+  k_mdot<<<kRedBlocks, kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w, c.partial);
+  k_mdot_finish<<<nb_(nv, 128), 128, 0, c.st>>>(nv, kRedBlocks, c.partial, c.hdev);
+  pie_status s = cuda_check(cudaMemcpyAsync(out_host, c.hdev, sizeof(cd) * nv, cudaMemcpyDeviceToHost, c.st), "dot");
+  if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "dot sync");
   return s;
+}
+
+// out = D Z D in.
+static pie_status scaled_op(Ctx& c, const cd* in, cd* out) {
+  k_scale<<<nb_(c.N, 256), 256, 0, c.st>>>(c.N, c.d, in, c.u);
+  pie_status s = apply_one(c.pr, c.u, out, c.st);
+  if (s != PIE_OK) return s;
+  k_scale<<<nb_(c.N, 256), 256, 0, c.st>>>(c.N, c.d, out, out);
+  return cuda_check(cudaGetLastError(), "gmres launch");
+}
+
+// y += sum_i coef[i] V[i] with host coefficients.
+static pie_status combine(Ctx& c, const cd* V, const std::vector<zc>& coef, int n, cd* y) {
+  std::vector<cd> h(n);
+  for (int i = 0; i < n; ++i) h[i] = cd{coef[i].real(), coef[i].imag()};
+  pie_status s = cuda_check(cudaMemcpyAsync(c.hdev, h.data(), sizeof(cd) * n, cudaMemcpyHostToDevice, c.st), "copy");
+  if (s != PIE_OK) return s;
+  k_mupdate<<<nb_(c.N, 256), 256, 0, c.st>>>(c.N, n, V, c.N, c.hdev, 1.0, y);
+  // the host vector must outlive the asynchronous copy
+  return cuda_check(cudaStreamSynchronize(c.st), "combine");
+}
+
+// One GMRES cycle (no restart) on the scaled operator, x0 = 0:
+// V[0] = r / ||r|| given in V; Arnoldi up to m steps or until the rotated
+// residual falls below stop_abs.  On return y (host) holds the coefficients,
+// j the number of steps, and `est` the rotated residual estimate.
+struct Cycle {
+  std::vector<zc> H, cs, sn, g, h, h2;
+  int m;
+  explicit Cycle(int m_) : H(size_t(m_ + 1) * m_), cs(m_), sn(m_), g(m_ + 1), h(m_ + 1), h2(m_ + 1), m(m_) {}
+};
+
+static pie_status arnoldi_cycle(Ctx& c, cd* V, cd* w, Cycle& cy, double beta, double stop_abs, int max_steps,
+                                int& j_out, std::vector<zc>& y, double& est, bool& breakdown, int& steps_done) {
+  const int64_t N = c.N;
+  const int m = cy.m;
+  pie_status s = PIE_OK;
+  std::fill(cy.H.begin(), cy.H.end(), zc(0));
+  std::fill(cy.g.begin(), cy.g.end(), zc(0));
+  cy.g[0] = beta;
+  int j = 0;
+  breakdown = false;
+  zc tmp[1];
+  for (; j < m && j < max_steps; ++j) {
+    cd* vj = V + size_t(j) * N;
+    if ((s = scaled_op(c, vj, w)) != PIE_OK) return s;
+    if ((s = dotc(c, j + 1, V, w, cy.h.data())) != PIE_OK) return s;
+    k_mupdate<<<nb_(N, 256), 256, 0, c.st>>>(N, j + 1, V, N, c.hdev, -1.0, w);
+    if ((s = dotc(c, j + 1, V, w, cy.h2.data())) != PIE_OK) return s;
+    k_mupdate<<<nb_(N, 256), 256, 0, c.st>>>(N, j + 1, V, N, c.hdev, -1.0, w);
+    for (int i = 0; i <= j; ++i) cy.h[i] += cy.h2[i];
+    if ((s = dotc(c, 1, w, w, tmp)) != PIE_OK) return s;
+    double hn = std::sqrt(tmp[0].real());
+    for (int i = 0; i <= j; ++i)
+      if (!std::isfinite(cy.h[i].real()) || !std::isfinite(cy.h[i].imag()) || !std::isfinite(hn)) {
+        set_error("pie_solve: non-finite Arnoldi coefficient");
+        return PIE_ERR_NAN;
+      }
+    for (int i = 0; i <= j; ++i) cy.H[size_t(i) * m + j] = cy.h[i];
+    // previous rotations, then a new one: G = [[conj c, conj s], [-s, c]]
+    for (int i = 0; i < j; ++i) {
+      zc a = cy.H[size_t(i) * m + j], b = cy.H[size_t(i + 1) * m + j];
+      cy.H[size_t(i) * m + j] = std::conj(cy.cs[i]) * a + std::conj(cy.sn[i]) * b;
+      cy.H[size_t(i + 1) * m + j] = -cy.sn[i] * a + cy.cs[i] * b;
+    }
+    zc a = cy.H[size_t(j) * m + j];
+    double den = std::sqrt(std::norm(a) + hn * hn);
+    cy.cs[j] = a / den;
+    cy.sn[j] = zc(hn / den);
+    cy.H[size_t(j) * m + j] = den;
+    cy.g[j + 1] = -cy.sn[j] * cy.g[j];
+    cy.g[j] = std::conj(cy.cs[j]) * cy.g[j];
+    ++steps_done;
+    if (hn <= 1e-14 * den) {
+      breakdown = true;
+      ++j;
+      break;
+    }
+    k_axs<<<nb_(N, 256), 256, 0, c.st>>>(N, 1.0 / hn, 0.0, w, V + size_t(j + 1) * N);
+    if (std::abs(cy.g[j + 1]) <= stop_abs) {
+      ++j;
+      break;
+    }
+  }
+  est = std::abs(cy.g[j]);
+  y.assign(j, zc(0));
+  for (int i = j - 1; i >= 0; --i) {
+    zc acc = cy.g[i];
+    for (int k = i + 1; k < j; ++k) acc -= cy.H[size_t(i) * m + k] * y[k];
+    y[i] = acc / cy.H[size_t(i) * m + i];
+  }
+  j_out = j;
+  return cuda_check(cudaGetLastError(), "arnoldi");
 }
 
 pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, int restart, pie_solve_stats* stats,
@@ -207,9 +310,11 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
   cd* w = wk.get<cd>(N, s);
   cd* u = wk.get<cd>(N, s);
   cd* r = wk.get<cd>(N, s);
+  cd* t = wk.get<cd>(N, s);
   cd* partial = wk.get<cd>(size_t(kRedBlocks) * (m + 1), s);
   cd* hdev = wk.get<cd>(m + 1, s);
   if (s != PIE_OK) return s;
+  Ctx c{pr, st, N, d, u, partial, hdev};
   const cd* b = static_cast<const cd*>(bv);
   cd* x = static_cast<cd*>(xv);
   const double w2e = pr.w * pr.w * eps0();
@@ -224,18 +329,15 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
   cudaMemsetAsync(x, 0, sizeof(cd) * N, st);
   cudaMemcpyAsync(r, b, sizeof(cd) * N, cudaMemcpyDeviceToDevice, st);
   zc tmp[1];
-  if ((s = dotc(N, 1, b, N, b, partial, hdev, tmp, st)) != PIE_OK) return s;
+  if ((s = dotc(c, 1, b, b, tmp)) != PIE_OK) return s;
   const double bn = std::sqrt(tmp[0].real());
   int it = 0;
-  double rel = 1.0;
-  pie_status result = PIE_ERR_NOCONV;
-  std::vector<zc> H(size_t(m + 1) * m), cs(m), sn(m), g(m + 1), h(m + 1), h2(m + 1);
-  if (bn == 0) {
-    result = PIE_OK;
-    rel = 0;
-  }
+  double rel = bn == 0 ? 0.0 : 1.0;
+  pie_status result = bn == 0 ? PIE_OK : PIE_ERR_NOCONV;
+  Cycle cy(m);
+  std::vector<zc> y;
   while (result != PIE_OK && it < maxit) {
-    if ((s = dotc(N, 1, r, N, r, partial, hdev, tmp, st)) != PIE_OK) return s;
+    if ((s = dotc(c, 1, r, r, tmp)) != PIE_OK) return s;
     rel = std::sqrt(tmp[0].real()) / bn;
     if (!std::isfinite(rel)) {
       set_error("pie_solve: non-finite residual");
@@ -245,88 +347,30 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
       result = PIE_OK;
       break;
     }
-    // scaled residual D r as the first Krylov vector
-    k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, r, V);
-    if ((s = dotc(N, 1, V, N, V, partial, hdev, tmp, st)) != PIE_OK) return s;
-    double beta = std::sqrt(tmp[0].real());
+    k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, r, V);  // scaled residual D r
+    if ((s = dotc(c, 1, V, V, tmp)) != PIE_OK) return s;
+    const double beta = std::sqrt(tmp[0].real());
     k_axs<<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / beta, 0.0, V, V);
-    std::fill(H.begin(), H.end(), zc(0));
-    std::fill(g.begin(), g.end(), zc(0));
-    g[0] = beta;
     int j = 0;
+    double est = 0;
     bool breakdown = false;
-    const double dbn = beta / rel;  // ~ ||D b|| scale for the inner estimate
-    for (; j < m && it < maxit; ++j) {
-      cd* vj = V + size_t(j) * N;
-      k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, vj, u);
-      if ((s = apply_one(pr, u, w, st)) != PIE_OK) return s;
-      k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, w, w);
-      // classical Gram-Schmidt, twice
-      if ((s = dotc(N, j + 1, V, N, w, partial, hdev, h.data(), st)) != PIE_OK) return s;
-      k_mupdate<<<nb_(N, 256), 256, 0, st>>>(N, j + 1, V, N, hdev, -1.0, w);
-      if ((s = dotc(N, j + 1, V, N, w, partial, hdev, h2.data(), st)) != PIE_OK) return s;
-      k_mupdate<<<nb_(N, 256), 256, 0, st>>>(N, j + 1, V, N, hdev, -1.0, w);
-      for (int i = 0; i <= j; ++i) h[i] += h2[i];
-      if ((s = dotc(N, 1, w, N, w, partial, hdev, tmp, st)) != PIE_OK) return s;
-      double hn = std::sqrt(tmp[0].real());
-      for (int i = 0; i <= j; ++i)
-        if (!std::isfinite(h[i].real()) || !std::isfinite(h[i].imag())) {
-          set_error("pie_solve: non-finite Arnoldi coefficient");
-          return PIE_ERR_NAN;
-        }
-      for (int i = 0; i <= j; ++i) H[size_t(i) * m + j] = h[i];
-      H[size_t(j + 1) * m + j] = hn;
-      // previous rotations, then a new one: G = [[conj c, conj s], [-s, c]]
-      for (int i = 0; i < j; ++i) {
-        zc a = H[size_t(i) * m + j], c2 = H[size_t(i + 1) * m + j];
-        H[size_t(i) * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * c2;
-        H[size_t(i + 1) * m + j] = -sn[i] * a + cs[i] * c2;
-      }
-      zc a = H[size_t(j) * m + j];
-      double den = std::sqrt(std::norm(a) + hn * hn);
-      cs[j] = a / den;
-      sn[j] = zc(hn / den);
-      H[size_t(j) * m + j] = den;
-      H[size_t(j + 1) * m + j] = 0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = std::conj(cs[j]) * g[j];
-      ++it;
-      if (hn <= 1e-14 * den) {
-        breakdown = true;
-        ++j;
-        break;
-      }
-      k_axs<<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / hn, 0.0, w, V + size_t(j + 1) * N);
-      if (std::abs(g[j + 1]) <= 0.5 * tol * dbn) {
-        ++j;
-        break;
-      }
-    }
-    // y = H^-1 g (upper triangular), x += D V y
-    std::vector<zc> y(j);
-    for (int i = j - 1; i >= 0; --i) {
-      zc acc = g[i];
-      for (int k = i + 1; k < j; ++k) acc -= H[size_t(i) * m + k] * y[k];
-      y[i] = acc / H[size_t(i) * m + i];
-    }
-    std::vector<cd> yh(j);
-    for (int i = 0; i < j; ++i) yh[i] = cd{y[i].real(), y[i].imag()};
-    cudaMemcpyAsync(hdev, yh.data(), sizeof(cd) * j, cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(u, 0, sizeof(cd) * N, st);
-    k_mupdate<<<nb_(N, 256), 256, 0, st>>>(N, j, V, N, hdev, 1.0, u);
-    k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, u, u);
+    const double dbn = beta / rel;  // scale of ||D b|| for the inner estimate
+    if ((s = arnoldi_cycle(c, V, w, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, est, breakdown, it)) != PIE_OK)
+      return s;
+    // x += D (sum_j y_j V_j)
+    cudaMemsetAsync(t, 0, sizeof(cd) * N, st);
+    if ((s = combine(c, V, y, j, t)) != PIE_OK) return s;
+    k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, t, t);
     {
-      // x += u
-      cd one = {1.0, 0.0};
-      cudaMemcpyAsync(hdev, &one, sizeof(cd), cudaMemcpyHostToDevice, st);
-      k_mupdate<<<nb_(N, 256), 256, 0, st>>>(N, 1, u, N, hdev, 1.0, x);
+      std::vector<zc> one(1, zc(1.0));
+      if ((s = combine(c, t, one, 1, x)) != PIE_OK) return s;
     }
     // true residual r = b - Z x
     if ((s = apply_one(pr, x, w, st)) != PIE_OK) return s;
     k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, w, r);
     if ((s = cuda_check(cudaGetLastError(), "gmres launch")) != PIE_OK) return s;
     if (breakdown) {
-      if ((s = dotc(N, 1, r, N, r, partial, hdev, tmp, st)) != PIE_OK) return s;
+      if ((s = dotc(c, 1, r, r, tmp)) != PIE_OK) return s;
       rel = std::sqrt(tmp[0].real()) / bn;
       result = rel <= tol ? PIE_OK : PIE_ERR_BREAKDOWN;
       if (result != PIE_OK) set_error("pie_solve: Arnoldi breakdown before convergence");
@@ -334,7 +378,7 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
     }
   }
   if (result != PIE_OK && result != PIE_ERR_BREAKDOWN) {
-    if ((s = dotc(N, 1, r, N, r, partial, hdev, tmp, st)) != PIE_OK) return s;
+    if ((s = dotc(c, 1, r, r, tmp)) != PIE_OK) return s;
     rel = std::sqrt(tmp[0].real()) / bn;
     if (rel <= tol)
       result = PIE_OK;

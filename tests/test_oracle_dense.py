@@ -98,3 +98,17 @@ def test_sphere_rcs_matches_mie():
     assert db.max() < 0.1
     # the E-plane null (scattering angle 60 deg) is resolved
     assert 10 * np.log10(s[120] / s.max()) < -60
+
+
+def test_rows_with_pair_mask_match_masked_matrix(small):
+    top, _ = small
+    c = top.centroid
+
+    def mask(t, s):
+        return np.linalg.norm(c[s] - c[t], axis=-1) < 0.6
+
+    Zn = assemble(top, 0.5, pair_mask=lambda t, s: mask(t, s[None, :] if np.ndim(s) == 0 else s)
+                  if np.ndim(t) == 0 else np.linalg.norm(c[s] - c[t], axis=-1) < 0.6)
+    x = pi.complex_normal(top.N, 12)
+    which = [1, 40, top.E + 3, top.N - 2]
+    assert np.allclose(rows(top, 0.5, which, x, pair_mask=mask), (Zn @ x)[which], rtol=1e-12)
