@@ -321,10 +321,16 @@ pie_status pie_problem_stage(pie_problem* h, int which, int level, double* out, 
     set_error("unknown stage");
     return PIE_ERR_PARAM;
   }
-  if (!f32) return cuda_check(cudaMemcpy(out, src, n * sizeof(cd), cudaMemcpyDeviceToHost), "stage copy");
-  std::vector<float> tmp(2 * n);
-  s = cuda_check(cudaMemcpy(tmp.data(), src, n * sizeof(cf), cudaMemcpyDeviceToHost), "stage copy");
-  for (size_t i = 0; i < 2 * n; ++i) out[i] = tmp[i];
+  std::vector<double> buf(2 * n);
+  if (!f32) {
+    s = cuda_check(cudaMemcpy(buf.data(), src, n * sizeof(cd), cudaMemcpyDeviceToHost), "stage copy");
+  } else {
+    std::vector<float> tmp(2 * n);
+    s = cuda_check(cudaMemcpy(tmp.data(), src, n * sizeof(cf), cudaMemcpyDeviceToHost), "stage copy");
+    for (size_t i = 0; i < 2 * n; ++i) buf[i] = tmp[i];
+  }
+  if (s != PIE_OK) return s;
+  std::memcpy(out, buf.data(), sizeof(double) * 2 * n);
   return s;
 }
 

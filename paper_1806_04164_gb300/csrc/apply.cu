@@ -49,7 +49,8 @@ __global__ void k_coef(int64_t T, int64_t E, const C2<Rio>* __restrict__ x, cons
 // a1: near part.  One warp per test triangle t; lanes run over the source
 // triangles of the neighbouring leaf boxes (contiguous in tree order), whose
 // eight pair moments are stored plane by plane ([8][nnz]), so a warp reads
-// 32 consecutive entries of each plane.  Writes pot[t] (initialises it).
+// 32 consecutive entries of each plane (measured faster than per-pair
+// records with vector loads).  Writes pot[t] (initialises it).
 template <typename Rm, typename Rio>
 __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int32_t* __restrict__ leaf_of,
                                               const int32_t* __restrict__ leaf_start,
@@ -250,10 +251,13 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
     const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Sc,
     const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Sp) {
   constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch;
+  // rows padded by one element (AP, BP) so that lanes striding over rows hit
+  // distinct shared-memory banks
+  constexpr int AP = NT + 1, BP = NPHI + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);  // spectra [slot][c][m][i], then results [slot][c][p]
-  C2<Rf>* B = A + NB * kComp * P;                     // filtered spectra [slot][c][i][m]
-  C2<Rf>* acc = B + NB * kComp * P;                   // parent pattern [c][p]
+  C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);  // spectra [slot][c][m][i (AP)], then results [slot][c][i][j (BP)]
+  C2<Rf>* B = A + NB * kComp * NPHI * AP;             // filtered spectra [slot][c][i][m (BP)]
+  C2<Rf>* acc = B + NB * kComp * NT * BP;             // parent pattern [c][p]
   C2<Rf>* tw = acc + kComp * P;                       // twiddles
   Rf* K = reinterpret_cast<Rf*>(tw + NPHI / 2);       // K_m blocks
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -277,20 +281,20 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
         for (int j = 0; j < NPHI; ++j) x[j] = src[j];
         fft_reg<NPHI>(x, tw, false);
 #pragma unroll
-        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * NT + i] = x[m];
+        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * AP + i] = x[m];
       }
     }
     __syncthreads();
     for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // K_m blocks
       const int sc = it / NPHI, m = it % NPHI;
-      const C2<Rf>* a = A + (sc * NPHI + m) * NT;
+      const C2<Rf>* a = A + (sc * NPHI + m) * AP;
       const Rf* Km = K + m * NT * NT;
 #pragma unroll
       for (int i = 0; i < NT; ++i) {
         C2<Rf> t = mk<Rf>(0, 0);
 #pragma unroll
         for (int k = 0; k < NT; ++k) rfma(t, Km[i * NT + k], a[k]);
-        B[(sc * NT + i) * NPHI + m] = t;
+        B[(sc * NT + i) * BP + m] = t;
       }
     }
     __syncthreads();
@@ -298,21 +302,22 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
       const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
       if (slot < nb) {
         C2<Rf> x[NPHI];
-        const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * NPHI;
+        const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * BP;
 #pragma unroll
         for (int m = 0; m < NPHI; ++m) x[m] = src[m];
         fft_reg<NPHI>(x, tw, true);
         const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
-        C2<Rf>* dst = A + (slot * kComp + c) * P + i * NPHI;
+        C2<Rf>* dst = A + ((slot * kComp + c) * NT + i) * BP;
 #pragma unroll
         for (int j = 0; j < NPHI; ++j) dst[j] = cmul(ph[j], x[j]);
       }
     }
     __syncthreads();
     for (int i = tid; i < kComp * P; i += nth) {
+      const int row = i / NPHI, j = i % NPHI;  // row = c * NT + theta row
       C2<Rf> v = acc[i];
       for (int slot = 0; slot < nb; ++slot) {
-        C2<Rf> u = A[slot * kComp * P + i];
+        C2<Rf> u = A[(slot * kComp * NT + row) * BP + j];
         v.x += u.x;
         v.y += u.y;
       }
@@ -330,10 +335,11 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
     const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Gp,
     const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Gc) {
   constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch;
+  constexpr int AP = NT + 1, BP = NPHI + 1;  // padded rows (bank spreading)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);
-  C2<Rf>* B = A + NB * kComp * P;
-  C2<Rf>* tw = B + NB * kComp * P;
+  C2<Rf>* B = A + NB * kComp * NPHI * AP;
+  C2<Rf>* tw = B + NB * kComp * NT * BP;
   Rf* K = reinterpret_cast<Rf*>(tw + NPHI / 2);
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int i = tid; i < NPHI * NT * NT; i += nth) K[i] = Kf[i];
@@ -359,20 +365,20 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
         }
         fft_reg<NPHI>(x, tw, false);
 #pragma unroll
-        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * NT + i] = x[m];
+        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * AP + i] = x[m];
       }
     }
     __syncthreads();
     for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // transposed K_m blocks
       const int sc = it / NPHI, m = it % NPHI;
-      const C2<Rf>* a = A + (sc * NPHI + m) * NT;
+      const C2<Rf>* a = A + (sc * NPHI + m) * AP;
       const Rf* Km = K + m * NT * NT;
 #pragma unroll
       for (int i = 0; i < NT; ++i) {
         C2<Rf> t = mk<Rf>(0, 0);
 #pragma unroll
         for (int k = 0; k < NT; ++k) rfma(t, Km[k * NT + i], a[k]);
-        B[(sc * NT + i) * NPHI + m] = t;
+        B[(sc * NT + i) * BP + m] = t;
       }
     }
     __syncthreads();
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
       const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
       if (slot < nb) {
         C2<Rf> x[NPHI];
-        const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * NPHI;
+        const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * BP;
 #pragma unroll
         for (int m = 0; m < NPHI; ++m) x[m] = src[m];
         fft_reg<NPHI>(x, tw, true);
@@ -554,7 +560,8 @@ void prof_mark(Problem& pr, int stage, bool end, cudaStream_t st) {
 template <int NT, typename Rf>
 static size_t fft_smem(bool interp) {
   constexpr int NPHI = 2 * NT, P = NT * NPHI;
-  return sizeof(C2<Rf>) * (2 * kFftBatch * kComp * P + (interp ? kComp * P : 0) + NPHI / 2) +
+  return sizeof(C2<Rf>) * (kFftBatch * kComp * NPHI * (NT + 1) + kFftBatch * kComp * NT * (NPHI + 1) +
+                           (interp ? kComp * P : 0) + NPHI / 2) +
          sizeof(Rf) * NPHI * NT * NT;
 }
 
