@@ -155,6 +155,16 @@ pie_status pie_problem_near(const pie_problem* pr, int64_t* nlist, int64_t* ptr,
  * PIE_ERR_CUDA. */
 pie_status pie_apply(pie_problem* pr, const void* x, void* y, int nrhs, int dtype, void* stream);
 
+/* y = Z^T x (conj = 0) or y = Z^H x (conj = 1), same arguments and errors as
+ * pie_apply.  The Galerkin operator of Eqs. (1)-(2) is complex symmetric
+ * (reciprocity); the discrete one keeps that: the near pair moments are
+ * two-sided, and the far part is symmetric on the antipodal angular grid
+ * (aggregation and disaggregation are each other's transposes, anterpolation
+ * is the transposed interpolation, T_{-w}(k) = T_w(-k)).  Z^T x therefore runs
+ * the forward stages (equal to Z x up to the far part's rounding, ~1e-5), and
+ * Z^H x = conj(Z conj x).  Uses one N-vector of library scratch. */
+pie_status pie_apply_t(pie_problem* pr, const void* x, void* y, int nrhs, int dtype, int conj, void* stream);
+
 /* y = Z_near x: the near part of the product alone (Section 3: interactions
  * of triangles in neighbouring leaf boxes, one-box buffer, computed exactly
  * as in the dense matrix).  Same arguments and errors as pie_apply.  Useful
@@ -220,6 +230,14 @@ pie_status pie_rhs_planewave(pie_problem* pr, const double khat[3], const double
  * (problem dtype). */
 pie_status pie_farfield(pie_problem* pr, const void* x, const double* rhat, int64_t ndir, void* E,
                         void* stream);
+
+/* Adjoint of the far-field map of pie_farfield: u = F^H E for E (device,
+ * ndir x 3 complex double) at the host directions rhat (ndir x 3); u:
+ * device, N complex of the problem's dtype (pulse entries are zero: the far
+ * zone depends on J only, Section 2).  Used for gradients of far-field
+ * objectives through an adjoint solve. */
+pie_status pie_farfield_adjoint(pie_problem* pr, const double* rhat, int64_t ndir, const void* E, void* u,
+                                void* stream);
 
 /* GMRES (Section 4) on Z x = b, zero initial guess, restarted every
  * `restart` steps, stopping when the FP64 residual ||b - Z x||/||b|| <= tol

@@ -14,7 +14,10 @@ Rules (readings; the paper does not state its integration rules):
 * near-singular pairs, defined by |c_t - c_s|^2 < 2.25 max(h_t^2, h_s^2) with h
   the longest edge of a triangle: outer 64-point (8 x 8) collapsed Gauss rule on t; the
   inner integral over s split as 1/(4 pi R) (closed form, oracle.singular) plus
-  (exp(i k R) - 1)/(4 pi R) by the 7-point rule.
+  (exp(i k R) - 1)/(4 pi R) by the 7-point rule; the rule is applied in both
+  orders and averaged (m0, mts symmetric; mt(t,s) with ms(s,t)), so that the
+  discrete operator keeps the reciprocity Z^T = Z of the continuous Galerkin
+  operator (the one-sided rule breaks it at ~1e-4).
 The squared distances and edge lengths are formed as ((x*x + y*y) + z*z) in
 IEEE double without fused multiply-add, so the classification is reproducible.
 
@@ -113,6 +116,13 @@ def singular_moments(geo: Geometry, k, t, s):
     return m0, mt, ms, mts
 
 
+def symmetric_singular_moments(geo: Geometry, k, t, s):
+    """The near-singular rule averaged over both orders of the pair."""
+    a0, at, as_, ats = singular_moments(geo, k, t, s)
+    b0, bt, bs, bts = singular_moments(geo, k, s, t)
+    return 0.5 * (a0 + b0), 0.5 * (at + bs), 0.5 * (as_ + bt), 0.5 * (ats + bts)
+
+
 def pair_moments(geo: Geometry, k, t, s, chunk=8000):
     """Moments for pair arrays (t test, s source) with the rule chosen by
     is_near_singular.  Returns m0 [P], mt [P,3], ms [P,3], mts [P] complex."""
@@ -124,7 +134,7 @@ def pair_moments(geo: Geometry, k, t, s, chunk=8000):
     ms = np.zeros((P, 3), np.complex128)
     mts = np.zeros(P, np.complex128)
     near = is_near_singular(geo.cent, geo.h2, t, s)
-    for mask, rule in ((near, singular_moments), (~near, regular_moments)):
+    for mask, rule in ((near, symmetric_singular_moments), (~near, regular_moments)):
         idx = np.nonzero(mask)[0]
         for a in range(0, idx.size, chunk):
             sl = idx[a:a + chunk]

@@ -50,7 +50,8 @@ _lib = None
 EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_destroy", "pie_mesh_info",
            "pie_mesh_edges", "pie_problem_create", "pie_problem_destroy", "pie_problem_info", "pie_problem_perm",
            "pie_problem_level", "pie_problem_near", "pie_apply", "pie_apply_near", "pie_problem_stage", "pie_rhs_planewave",
-           "pie_farfield", "pie_solve", "pie_profile_begin", "pie_profile_end", "pie_apply_near_noalloc"]
+           "pie_farfield", "pie_solve", "pie_profile_begin", "pie_profile_end", "pie_apply_near_noalloc", "pie_apply_t",
+           "pie_farfield_adjoint"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -81,6 +82,8 @@ def lib():
         L.pie_apply.argtypes = [vp, vp, vp, i32, i32, vp]
         L.pie_apply_near.argtypes = [vp, vp, vp, i32, i32, vp]
         L.pie_apply_near_noalloc.argtypes = [vp, vp, vp, i32, vp]
+        L.pie_apply_t.argtypes = [vp, vp, vp, i32, i32, i32, vp]
+        L.pie_farfield_adjoint.argtypes = [vp, PD, i64, vp, vp, vp]
         L.pie_problem_stage.argtypes = [vp, i32, i32, PD, vp]
         L.pie_rhs_planewave.argtypes = [vp, PD, PD, dbl, vp, i32, vp]
         L.pie_farfield.argtypes = [vp, vp, PD, i64, vp, vp]
@@ -98,6 +101,11 @@ def _check(code):
 
 def _ptr(a, ctype):
     return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _dense(t):
+    """Materialise lazy conjugate / negative views: the C ABI reads raw memory."""
+    return t.resolve_conj().resolve_neg().contiguous()
 
 
 def _stream(stream):
@@ -196,7 +204,8 @@ class Problem:
         """y = Z x for device tensors of shape [N] or [nrhs, N] (row j = right-hand
         side j); near_only=True applies the near part Z_near alone."""
         import torch
-        assert x.is_cuda and x.dtype == self.torch_dtype and x.is_contiguous()
+        x = _dense(x)
+        assert x.is_cuda and x.dtype == self.torch_dtype
         if y is None:
             y = torch.empty_like(x)
         nrhs = 1 if x.dim() == 1 else x.shape[0]
@@ -215,6 +224,29 @@ class Problem:
         n = ctypes.c_int32()
         _check(lib().pie_profile_end(self.handle, _ptr(ms, ctypes.c_double), ctypes.byref(n)))
         return dict(zip(STAGES, ms.tolist())), n.value
+
+    def apply_t(self, x, conj=False, y=None, stream=None):
+        """y = Z^T x, or Z^H x with conj=True (pie_apply_t)."""
+        import torch
+        x = _dense(x)
+        assert x.is_cuda and x.dtype == self.torch_dtype
+        if y is None:
+            y = torch.empty_like(x)
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        _check(lib().pie_apply_t(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), nrhs,
+                                 self.dtype_code, 1 if conj else 0, _stream(stream)))
+        return y
+
+    def farfield_adjoint(self, E, rhat, stream=None):
+        """u = F^H E (pie_farfield_adjoint)."""
+        import torch
+        rh = np.ascontiguousarray(rhat, np.float64)
+        E = _dense(E)
+        u = torch.empty(self.N, dtype=self.torch_dtype, device="cuda")
+        _check(lib().pie_farfield_adjoint(self.handle, _ptr(rh, ctypes.c_double), rh.shape[0],
+                                          ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                          _stream(stream)))
+        return u
 
     def stage(self, which, level=0, stream=None):
         if which in (0, 1):
@@ -248,6 +280,7 @@ class Problem:
     def farfield(self, x, rhat, stream=None):
         import torch
         rh = np.ascontiguousarray(rhat, np.float64)
+        x = _dense(x)
         E = torch.empty((rh.shape[0], 3), dtype=torch.complex128, device="cuda")
         _check(lib().pie_farfield(self.handle, ctypes.c_void_p(x.data_ptr()), _ptr(rh, ctypes.c_double),
                                   rh.shape[0], ctypes.c_void_p(E.data_ptr()), _stream(stream)))
@@ -256,6 +289,7 @@ class Problem:
     def solve(self, b, tol=1e-6, maxit=1000, restart=100, stream=None):
         """Restarted GMRES on Z x = b (pie_solve)."""
         import torch
+        b = _dense(b)
         x = torch.zeros_like(b)
         st = SolveStats()
         code = lib().pie_solve(self.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), tol,

@@ -241,6 +241,35 @@ pie_status pie_apply_near(pie_problem* h, const void* x, void* y, int nrhs, int 
   return apply_cols(h, x, y, nrhs, dtype, stream, true);
 }
 
+pie_status pie_apply_t(pie_problem* h, const void* x, void* y, int nrhs, int dtype, int conj, void* stream) {
+  if (!h || (!x && nrhs > 0) || (!y && nrhs > 0) || nrhs < 0 || (conj != 0 && conj != 1)) {
+    set_error("pie_apply_t: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  Problem& pr = h->p;
+  if (dtype != (pr.io_f32() ? PIE_C64 : PIE_C128)) {
+    set_error("pie_apply_t: dtype does not match the problem precision");
+    return PIE_ERR_PARAM;
+  }
+  size_t es = pr.io_f32() ? sizeof(cf) : sizeof(cd);
+  for (int j = 0; j < nrhs; ++j) {
+    pie_status s = apply_t_one(pr, static_cast<const char*>(x) + es * size_t(pr.N) * j,
+                               static_cast<char*>(y) + es * size_t(pr.N) * j, conj == 1,
+                               static_cast<cudaStream_t>(stream));
+    if (s != PIE_OK) return s;
+  }
+  return PIE_OK;
+}
+
+pie_status pie_farfield_adjoint(pie_problem* h, const double* rhat, int64_t ndir, const void* E, void* u,
+                                void* stream) {
+  if (!h || !rhat || !E || !u || ndir < 1) {
+    set_error("pie_farfield_adjoint: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  return farfield_adjoint(h->p, rhat, ndir, E, u, static_cast<cudaStream_t>(stream));
+}
+
 pie_status pie_profile_begin(pie_problem* h, int max_applies) {
   if (!h || max_applies < 1) {
     set_error("pie_profile_begin: invalid argument");

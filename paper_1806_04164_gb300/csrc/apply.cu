@@ -885,3 +885,110 @@ pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, v
 }
 
 }  // namespace pie
+
+namespace pie {
+
+// ---------------------------------------------------------------- adjoint
+
+template <typename R>
+__global__ void k_conj(int64_t n, const C2<R>* __restrict__ x, C2<R>* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = mk<R>(x[i].x, -x[i].y);
+}
+
+// y = Z^T x (conj = false) or Z^H x = conj(Z conj x) (conj = true).  The
+// discrete operator is complex symmetric -- the near pair moments by the
+// two-sided near-singular rule, the far part by the antipodal angular grid
+// (aggregation and disaggregation are each other's transposes, F^T is the
+// anterpolation of F, T_{-w}(k) = T_w(-k)) -- so Z^T x runs the same stages.
+pie_status apply_t_one(Problem& pr, const void* x, void* y, bool conj, cudaStream_t st) {
+  if (!conj) return apply_one(pr, x, y, st);
+  const int64_t N = pr.N;
+  if (pr.io_f32()) {
+    k_conj<float><<<nblk(N, 256), 256, 0, st>>>(N, static_cast<const cf*>(x), static_cast<cf*>(pr.vec));
+    pie_status s = apply_one(pr, pr.vec, y, st);
+    if (s != PIE_OK) return s;
+    k_conj<float><<<nblk(N, 256), 256, 0, st>>>(N, static_cast<const cf*>(y), static_cast<cf*>(y));
+  } else {
+    k_conj<double><<<nblk(N, 256), 256, 0, st>>>(N, static_cast<const cd*>(x), static_cast<cd*>(pr.vec));
+    pie_status s = apply_one(pr, pr.vec, y, st);
+    if (s != PIE_OK) return s;
+    k_conj<double><<<nblk(N, 256), 256, 0, st>>>(N, static_cast<const cd*>(y), static_cast<cd*>(y));
+  }
+  return cuda_check(cudaGetLastError(), "adjoint launch");
+}
+
+// Adjoint of the far-field map x -> E (Section 2 far zone): with
+// h(r) = sum_d conj(i w mu0 / 4 pi) exp(+i k rhat_d . r) (I - rhat_d rhat_d) E_d,
+// (F^H E)_m = sum_{t in m} c_t,m int_t (r - p_m) . h(r) dr, i.e. the Galerkin
+// testing of the potentials U = int (r - c_t).h, V = int h (T1 = T2 = 0).
+template <typename Rio>
+__global__ void k_farfield_adj(int64_t T, int64_t ndir, const double* __restrict__ vert,
+                               const double* __restrict__ cent, const double* __restrict__ area,
+                               const double* __restrict__ rhat, const cd* __restrict__ E, double k0, double pref,
+                               const double* __restrict__ rule, C2<Rio>* __restrict__ pot) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const double* v = vert + 9 * t;
+  double Ur = 0, Ui = 0, Vr[3] = {0, 0, 0}, Vi[3] = {0, 0, 0};
+  for (int q = 0; q < 7; ++q) {
+    double r[3];
+    for (int d = 0; d < 3; ++d) r[d] = rule[4 * q] * v[d] + rule[4 * q + 1] * v[3 + d] + rule[4 * q + 2] * v[6 + d];
+    const double wq = rule[4 * q + 3] * area[t];
+    double hr[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int64_t dd = 0; dd < ndir; ++dd) {
+      const double* rh = rhat + 3 * dd;
+      const cd* e = E + 3 * dd;
+      double er_ = rh[0] * e[0].x + rh[1] * e[1].x + rh[2] * e[2].x;
+      double ei_ = rh[0] * e[0].y + rh[1] * e[1].y + rh[2] * e[2].y;
+      double s, c;
+      sincos(k0 * (rh[0] * r[0] + rh[1] * r[1] + rh[2] * r[2]), &s, &c);
+      for (int d = 0; d < 3; ++d) {
+        double pr_ = e[d].x - rh[d] * er_, pi_ = e[d].y - rh[d] * ei_;  // (I - rr) E
+        hr[d] += c * pr_ - s * pi_;
+        hi[d] += c * pi_ + s * pr_;
+      }
+    }
+    // times conj(i pref) = -i pref
+    for (int d = 0; d < 3; ++d) {
+      double a = pref * hi[d], b = -pref * hr[d];
+      double u = r[d] - cent[3 * t + d];
+      Ur += wq * u * a;
+      Ui += wq * u * b;
+      Vr[d] += wq * a;
+      Vi[d] += wq * b;
+    }
+  }
+  C2<Rio>* o = pot + 6 * t;
+  o[0] = mk<Rio>(Rio(Ur), Rio(Ui));
+  for (int d = 0; d < 3; ++d) o[1 + d] = mk<Rio>(Rio(Vr[d]), Rio(Vi[d]));
+  o[4] = mk<Rio>(0, 0);
+  o[5] = mk<Rio>(0, 0);
+}
+
+pie_status farfield_adjoint(Problem& pr, const double* rhat, int64_t ndir, const void* E, void* u, cudaStream_t st) {
+  double* d_rhat = nullptr;
+  pie_status s = cuda_check(cudaMallocAsync((void**)&d_rhat, sizeof(double) * 3 * ndir, st), "farfield alloc");
+  if (s != PIE_OK) return s;
+  s = cuda_check(cudaMemcpyAsync(d_rhat, rhat, sizeof(double) * 3 * ndir, cudaMemcpyHostToDevice, st), "copy");
+  if (s != PIE_OK) return s;
+  const double pref = pr.w * kMu0 / (4.0 * kPi);
+  if (pr.io_f32()) {
+    k_farfield_adj<float><<<nblk(pr.T, 128), 128, 0, st>>>(pr.T, ndir, pr.vert, pr.cent, pr.area, d_rhat,
+                                                           static_cast<const cd*>(E), pr.k0, pref, pr.rule7,
+                                                           static_cast<cf*>(pr.pot));
+    k_assemble<float><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                       pr.inv_perm, static_cast<cf*>(pr.pot), static_cast<cf*>(u));
+  } else {
+    k_farfield_adj<double><<<nblk(pr.T, 128), 128, 0, st>>>(pr.T, ndir, pr.vert, pr.cent, pr.area, d_rhat,
+                                                            static_cast<const cd*>(E), pr.k0, pref, pr.rule7,
+                                                            static_cast<cd*>(pr.pot));
+    k_assemble<double><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                        pr.inv_perm, static_cast<cd*>(pr.pot), static_cast<cd*>(u));
+  }
+  s = cuda_check(cudaGetLastError(), "farfield adjoint launch");
+  cudaFreeAsync(d_rhat, st);
+  return s;
+}
+
+}  // namespace pie

@@ -89,6 +89,7 @@ struct Problem {
   // work buffers
   void* coef = nullptr;          // [T][6] complex (io precision)
   void* coef32 = nullptr;        // [T][6] complex float copy for the MIXED near part
+  void* vec = nullptr;           // [N] complex (io precision), adjoint scratch
   void* pot = nullptr;           // [T][6]
 
   bool near_f32() const { return par.precision != PIE_FP64; }
@@ -108,6 +109,9 @@ pie_status rhs_planewave(Problem& pr, const double* khat, const double* pol, dou
                          cudaStream_t st);
 pie_status farfield(Problem& pr, const void* x, const double* rhat, int64_t ndir, void* E,
                     cudaStream_t st);
+pie_status apply_t_one(Problem& pr, const void* x, void* y, bool conj, cudaStream_t st);
+pie_status farfield_adjoint(Problem& pr, const double* rhat, int64_t ndir, const void* E, void* u,
+                            cudaStream_t st);
 pie_status solve(Problem& pr, const void* b, void* x, double tol, int maxit, int restart,
                  pie_solve_stats* stats, cudaStream_t st);
 

@@ -1,6 +1,7 @@
 // Operator set-up on the device, all in FP64 (Sections 2-3):
 //  - near pair moments of g over triangle pairs in neighbouring leaf boxes,
-//    with closed-form static inner integrals for near-singular pairs;
+//    with closed-form static inner integrals for near-singular pairs (rule
+//    averaged over both orders of the pair);
 //  - leaf radiation tables (Pi, M) at the leaf wavenumber kappa_L;
 //  - translation operators of Eq. (5) per level and offset;
 //  - interpolation filter (degree rescale) and phases.
@@ -210,9 +211,25 @@ __global__ void __launch_bounds__(128) k_near_build(int64_t T, int64_t nnz, cons
     for (int j = lane; j < ns; j += 32) {
       int64_t s = s0 + j;
       Moments m;
-      if (near_singular(ct, cent + 3 * s, h2[t], h2[s]))
+      if (near_singular(ct, cent + 3 * s, h2[t], h2[s])) {
+        // the one-sided rule averaged over both orders of the pair, so that
+        // the discrete operator keeps the reciprocity Z^T = Z
+        Moments m2;
         moments_singular(vt, ct, area[t], vert + 9 * s, cent + 3 * s, area[s], k, rule7, rule64, m);
-      else
+        moments_singular(vert + 9 * s, cent + 3 * s, area[s], vt, ct, area[t], k, rule7, rule64, m2);
+        m.m0r = 0.5 * (m.m0r + m2.m0r);
+        m.m0i = 0.5 * (m.m0i + m2.m0i);
+        m.mtsr = 0.5 * (m.mtsr + m2.mtsr);
+        m.mtsi = 0.5 * (m.mtsi + m2.mtsi);
+        for (int d = 0; d < 3; ++d) {
+          double tr = 0.5 * (m.mtr[d] + m2.msr[d]), ti = 0.5 * (m.mti[d] + m2.msi[d]);
+          double sr = 0.5 * (m.msr[d] + m2.mtr[d]), si = 0.5 * (m.msi[d] + m2.mti[d]);
+          m.mtr[d] = tr;
+          m.mti[d] = ti;
+          m.msr[d] = sr;
+          m.msi[d] = si;
+        }
+      } else
         moments_regular(vt, ct, area[t], vert + 9 * s, cent + 3 * s, area[s], k, rule7, m);
       int64_t ee = e + j;
       mom[ee] = mk<Rm>(Rm(m.m0r), Rm(m.m0i));
@@ -646,6 +663,7 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   pr.coef = zalloc(pr, cio * 6 * size_t(T), s);
   pr.pot = zalloc(pr, cio * 6 * size_t(T), s);
   if (pr.par.precision == PIE_MIXED) pr.coef32 = zalloc(pr, sizeof(cf) * 6 * size_t(T), s);
+  pr.vec = zalloc(pr, cio * size_t(pr.N), s);
   if (s != PIE_OK) return s;
   if ((s = cuda_check(cudaGetLastError(), "setup launch")) != PIE_OK) return s;
   return cuda_check(cudaStreamSynchronize(st), "setup");

@@ -81,3 +81,19 @@ def test_rejects_leaf_smaller_than_near_singular_radius():
     xyz, tri = pi.icosphere(2)
     with pytest.raises(ValueError):
         MLFMA(xyz, tri, 0.01, 4, side=2.0)
+
+
+def test_far_part_reciprocity():
+    """The discrete far part is complex symmetric in exact arithmetic: with
+    low-amplification parameters u^T M v = v^T M u to ~1e-13 (at the chosen
+    parameters the FP64 rounding amplification leaves ~1e-5)."""
+    xyz, tri = pi.icosphere(3)
+    M = MLFMA(xyz, tri, 0.01, 4, tau=3, x=0.4, ntheta=4, side=2.0)
+    u = pi.complex_normal(M.top.N, 1)
+    v = pi.complex_normal(M.top.N, 2)
+    a = u @ M.apply(v, near=False)
+    b = v @ M.apply(u, near=False)
+    assert abs(a - b) <= 1e-12 * abs(a)
+    an = u @ M.apply(v, far=False)
+    bn = v @ M.apply(u, far=False)
+    assert abs(an - bn) <= 1e-13 * abs(an)
