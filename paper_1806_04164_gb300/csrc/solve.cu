@@ -3,9 +3,10 @@
 // The system is scaled symmetrically, A = D Z D with D = |diag Z|^{-1/2}
 // (the diagonal comes from the near-part self and neighbour pair moments), so
 // that the RWG and pulse blocks, whose physical units differ, are balanced.
-// Arnoldi runs on the device in complex double with classical Gram-Schmidt
-// applied twice; dot products use fixed-order two-pass reductions (results do
-// not depend on scheduling).  The small Hessenberg problem (Givens rotations)
+// Arnoldi runs on the device in complex double with classical Gram-Schmidt,
+// repeated when the first pass cancels most of the vector (DGKS criterion);
+// dot products use fixed-order two-pass reductions (results do not depend on
+// scheduling).  The small Hessenberg problem (Givens rotations)
 // is solved on the host.  Stopping test: ||b - Z x|| / ||b|| <= tol on the
 // unscaled system, recomputed from the true residual at every restart.
 #include <chrono>
@@ -18,7 +19,6 @@
 namespace pie {
 
 typedef std::complex<double> zc;
-constexpr int kRedBlocks = 608;   // 4 x 152 SMs
 constexpr int kRedThreads = 256;
 
 static inline unsigned nb_(int64_t n, int b) { return unsigned((n + b - 1) / b); }
@@ -99,37 +99,36 @@ __global__ void k_axs(int64_t N, double ar, double ai, const cd* __restrict__ x,
   if (i < N) y[i] = mk<double>(ar * x[i].x - ai * x[i].y, ar * x[i].y + ai * x[i].x);
 }
 
-// partial[v][blk] = sum_{n in blk's slice} conj(V[v][n]) w[n], v < nv.
-// Pass 1 of a fixed-order reduction.
+// partial[v][tile] = sum over the tile's entries of conj(V[v][n]) w[n].
+// Pass 1 of a fixed-order reduction; grid = (tiles, vectors), so all vectors
+// are reduced in parallel.
+constexpr int kTile = 4096;
 __global__ void __launch_bounds__(kRedThreads) k_mdot(int64_t N, int nv, const cd* __restrict__ V, int64_t ldv,
                                                       const cd* __restrict__ w, cd* __restrict__ partial) {
   __shared__ double sr[kRedThreads / 32], si[kRedThreads / 32];
-  const int64_t per = (N + gridDim.x - 1) / gridDim.x;
-  const int64_t n0 = blockIdx.x * per, n1 = min(N, n0 + per);
-  for (int v = 0; v < nv; ++v) {
-    const cd* vv = V + v * ldv;
-    double ar = 0, ai = 0;
-    for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-      cd a = vv[n], b = w[n];
-      ar += a.x * b.x + a.y * b.y;
-      ai += a.x * b.y - a.y * b.x;
+  const int v = blockIdx.y;
+  const int64_t n0 = int64_t(blockIdx.x) * kTile, n1 = min(N, n0 + kTile);
+  const cd* vv = V + v * ldv;
+  double ar = 0, ai = 0;
+  for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+    cd a = vv[n], b = w[n];
+    ar += a.x * b.x + a.y * b.y;
+    ai += a.x * b.y - a.y * b.x;
+  }
+  ar = warp_sum(ar);
+  ai = warp_sum(ai);
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = ar;
+    si[threadIdx.x >> 5] = ai;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0, ti = 0;
+    for (int k = 0; k < kRedThreads / 32; ++k) {
+      tr += sr[k];
+      ti += si[k];
     }
-    ar = warp_sum(ar);
-    ai = warp_sum(ai);
-    if ((threadIdx.x & 31) == 0) {
-      sr[threadIdx.x >> 5] = ar;
-      si[threadIdx.x >> 5] = ai;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tr = 0, ti = 0;
-      for (int k = 0; k < kRedThreads / 32; ++k) {
-        tr += sr[k];
-        ti += si[k];
-      }
-      partial[(int64_t)v * gridDim.x + blockIdx.x] = mk<double>(tr, ti);
-    }
-    __syncthreads();
+    partial[(int64_t)v * gridDim.x + blockIdx.x] = mk<double>(tr, ti);
   }
 }
 
@@ -145,18 +144,22 @@ __global__ void k_mdot_finish(int nv, int nblk, const cd* __restrict__ partial, 
   out[v] = mk<double>(r, i);
 }
 
-// w -= sum_v h[v] V[v]   (or w += when sign = +1)
+// w -= sum_v h[v] V[v]   (or w += when sign = +1); h staged in shared memory.
 __global__ void k_mupdate(int64_t N, int nv, const cd* __restrict__ V, int64_t ldv, const cd* __restrict__ h,
                           double sign, cd* __restrict__ w) {
+  extern __shared__ cd hs[];
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) hs[v] = h[v];
+  __syncthreads();
   int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= N) return;
-  double r = w[n].x, i = w[n].y;
+  double r = 0, i = 0;
+#pragma unroll 4
   for (int v = 0; v < nv; ++v) {
-    cd a = V[v * ldv + n], c = h[v];
-    r += sign * (c.x * a.x - c.y * a.y);
-    i += sign * (c.x * a.y + c.y * a.x);
+    cd a = V[v * ldv + n], c = hs[v];
+    r += c.x * a.x - c.y * a.y;
+    i += c.x * a.y + c.y * a.x;
   }
-  w[n] = mk<double>(r, i);
+  w[n] = mk<double>(w[n].x + sign * r, w[n].y + sign * i);
 }
 
 // ---------------------------------------------------------------- host loop
@@ -194,8 +197,9 @@ struct Ctx {
 
 // conj(a) . b over N entries, deterministic; result on the host.
 static pie_status dotc(Ctx& c, int nv, const cd* V, const cd* w, zc* out_host) {
-  k_mdot<<<kRedBlocks, kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w, c.partial);
-  k_mdot_finish<<<nb_(nv, 128), 128, 0, c.st>>>(nv, kRedBlocks, c.partial, c.hdev);
+  const unsigned tiles = unsigned((c.N + kTile - 1) / kTile);
+  k_mdot<<<dim3(tiles, unsigned(nv)), kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w, c.partial);
+  k_mdot_finish<<<nb_(nv, 128), 128, 0, c.st>>>(nv, int(tiles), c.partial, c.hdev);
   pie_status s = cuda_check(cudaMemcpyAsync(out_host, c.hdev, sizeof(cd) * nv, cudaMemcpyDeviceToHost, c.st), "dot");
   if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "dot sync");
   return s;
@@ -216,7 +220,7 @@ static pie_status combine(Ctx& c, const cd* V, const std::vector<zc>& coef, int 
   for (int i = 0; i < n; ++i) h[i] = cd{coef[i].real(), coef[i].imag()};
   pie_status s = cuda_check(cudaMemcpyAsync(c.hdev, h.data(), sizeof(cd) * n, cudaMemcpyHostToDevice, c.st), "copy");
   if (s != PIE_OK) return s;
-  k_mupdate<<<nb_(c.N, 256), 256, 0, c.st>>>(c.N, n, V, c.N, c.hdev, 1.0, y);
+  k_mupdate<<<nb_(c.N, 256), 256, sizeof(cd) * n, c.st>>>(c.N, n, V, c.N, c.hdev, 1.0, y);
   // the host vector must outlive the asynchronous copy
   return cuda_check(cudaStreamSynchronize(c.st), "combine");
 }
@@ -245,13 +249,21 @@ static pie_status arnoldi_cycle(Ctx& c, cd* V, cd* w, Cycle& cy, double beta, do
   for (; j < m && j < max_steps; ++j) {
     cd* vj = V + size_t(j) * N;
     if ((s = scaled_op(c, vj, w)) != PIE_OK) return s;
+    // classical Gram-Schmidt; a second pass only when the first one cancelled
+    // most of w (Daniel-Gragg-Kaufman-Stewart criterion)
+    if ((s = dotc(c, 1, w, w, tmp)) != PIE_OK) return s;
+    const double wn0 = std::sqrt(tmp[0].real());
     if ((s = dotc(c, j + 1, V, w, cy.h.data())) != PIE_OK) return s;
-    k_mupdate<<<nb_(N, 256), 256, 0, c.st>>>(N, j + 1, V, N, c.hdev, -1.0, w);
-    if ((s = dotc(c, j + 1, V, w, cy.h2.data())) != PIE_OK) return s;
-    k_mupdate<<<nb_(N, 256), 256, 0, c.st>>>(N, j + 1, V, N, c.hdev, -1.0, w);
-    for (int i = 0; i <= j; ++i) cy.h[i] += cy.h2[i];
+    k_mupdate<<<nb_(N, 256), 256, sizeof(cd) * (j + 1), c.st>>>(N, j + 1, V, N, c.hdev, -1.0, w);
     if ((s = dotc(c, 1, w, w, tmp)) != PIE_OK) return s;
     double hn = std::sqrt(tmp[0].real());
+    if (hn < 0.7 * wn0) {
+      if ((s = dotc(c, j + 1, V, w, cy.h2.data())) != PIE_OK) return s;
+      k_mupdate<<<nb_(N, 256), 256, sizeof(cd) * (j + 1), c.st>>>(N, j + 1, V, N, c.hdev, -1.0, w);
+      for (int i = 0; i <= j; ++i) cy.h[i] += cy.h2[i];
+      if ((s = dotc(c, 1, w, w, tmp)) != PIE_OK) return s;
+      hn = std::sqrt(tmp[0].real());
+    }
     for (int i = 0; i <= j; ++i)
       if (!std::isfinite(cy.h[i].real()) || !std::isfinite(cy.h[i].imag()) || !std::isfinite(hn)) {
         set_error("pie_solve: non-finite Arnoldi coefficient");
@@ -311,7 +323,7 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
   cd* u = wk.get<cd>(N, s);
   cd* r = wk.get<cd>(N, s);
   cd* t = wk.get<cd>(N, s);
-  cd* partial = wk.get<cd>(size_t(kRedBlocks) * (m + 1), s);
+  cd* partial = wk.get<cd>(size_t((N + kTile - 1) / kTile) * (m + 2), s);
   cd* hdev = wk.get<cd>(m + 1, s);
   if (s != PIE_OK) return s;
   Ctx c{pr, st, N, d, u, partial, hdev};
