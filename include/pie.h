@@ -243,9 +243,13 @@ pie_status pie_farfield_adjoint(pie_problem* pr, const double* rhat, int64_t ndi
  * `restart` steps, stopping when the FP64 residual ||b - Z x||/||b|| <= tol
  * (the operator is scaled symmetrically by the inverse square roots of the
  * diagonal magnitudes of its near part; the stopping test is on the
- * unscaled system).  b, x: device, N complex of the problem's dtype.
- * Synchronises the stream.  Errors: PIE_ERR_NOCONV, PIE_ERR_BREAKDOWN,
- * PIE_ERR_NAN, PIE_ERR_CUDA. */
+ * unscaled system).  PIE_FP64 problems keep the Krylov basis in complex
+ * double; PIE_MIXED problems keep it in complex float, with the solution and
+ * the true residual in complex double recomputed at every restart (iterative
+ * refinement with a GMRES inner solver), so the basis precision limits the
+ * progress of a cycle, not the accuracy reached.  b, x: device, N complex
+ * double.  Synchronises the stream.  Errors: PIE_ERR_PARAM (PIE_FP32
+ * problem), PIE_ERR_NOCONV, PIE_ERR_BREAKDOWN, PIE_ERR_NAN, PIE_ERR_CUDA. */
 pie_status pie_solve(pie_problem* pr, const void* b, void* x, double tol, int maxit, int restart,
                      pie_solve_stats* stats, void* stream);
 

@@ -82,44 +82,47 @@ __global__ void k_diag_scale(int64_t N, int64_t E, int64_t nnz, const int32_t* _
   dscale[i] = a > 0 ? 1.0 / sqrt(a) : 1.0;
 }
 
-__global__ void k_scale(int64_t N, const double* __restrict__ d, const cd* __restrict__ x, cd* __restrict__ y) {
+// y = d x, converting between the Krylov basis type and complex double.
+template <typename A, typename B>
+__global__ void k_scale(int64_t N, const double* __restrict__ d, const C2<A>* __restrict__ x, C2<B>* __restrict__ y) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < N) y[i] = mk<double>(d[i] * x[i].x, d[i] * x[i].y);
+  if (i < N) y[i] = mk<B>(B(d[i] * double(x[i].x)), B(d[i] * double(x[i].y)));
 }
 
-// y = a - b (elementwise)
+// y = a - b (elementwise, complex double)
 __global__ void k_sub(int64_t N, const cd* __restrict__ a, const cd* __restrict__ b, cd* __restrict__ y) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < N) y[i] = mk<double>(a[i].x - b[i].x, a[i].y - b[i].y);
 }
 
-// y = alpha x
-__global__ void k_axs(int64_t N, double ar, double ai, const cd* __restrict__ x, cd* __restrict__ y) {
+// y = alpha x (real alpha)
+template <typename B>
+__global__ void k_axs(int64_t N, double alpha, const C2<B>* __restrict__ x, C2<B>* __restrict__ y) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < N) y[i] = mk<double>(ar * x[i].x - ai * x[i].y, ar * x[i].y + ai * x[i].x);
+  if (i < N) y[i] = mk<B>(B(alpha * double(x[i].x)), B(alpha * double(x[i].y)));
 }
 
-// partial[v][tile] = sum over the tile's entries of conj(V[v][n]) w[n].
-// Pass 1 of a fixed-order reduction; grid = (tiles, vectors), so all vectors
-// are reduced in parallel.
+// partial[v][tile] = sum over the tile's entries of conj(V[v][n]) w[n]
+// (accumulated in the basis type inside a tile, then in double).  Pass 1 of a
+// fixed-order reduction; grid = (tiles, vectors), all vectors in parallel.
 constexpr int kTile = 4096;
-__global__ void __launch_bounds__(kRedThreads) k_mdot(int64_t N, int nv, const cd* __restrict__ V, int64_t ldv,
-                                                      const cd* __restrict__ w, cd* __restrict__ partial) {
+template <typename B>
+__global__ void __launch_bounds__(kRedThreads) k_mdot(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv,
+                                                      const C2<B>* __restrict__ w, cd* __restrict__ partial) {
   __shared__ double sr[kRedThreads / 32], si[kRedThreads / 32];
   const int v = blockIdx.y;
   const int64_t n0 = int64_t(blockIdx.x) * kTile, n1 = min(N, n0 + kTile);
-  const cd* vv = V + v * ldv;
-  double ar = 0, ai = 0;
+  const C2<B>* vv = V + v * ldv;
+  B ar = 0, ai = 0;
   for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-    cd a = vv[n], b = w[n];
+    C2<B> a = vv[n], b = w[n];
     ar += a.x * b.x + a.y * b.y;
     ai += a.x * b.y - a.y * b.x;
   }
-  ar = warp_sum(ar);
-  ai = warp_sum(ai);
+  double dr = warp_sum(double(ar)), di = warp_sum(double(ai));
   if ((threadIdx.x & 31) == 0) {
-    sr[threadIdx.x >> 5] = ar;
-    si[threadIdx.x >> 5] = ai;
+    sr[threadIdx.x >> 5] = dr;
+    si[threadIdx.x >> 5] = di;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(kRedThreads) k_mdot(int64_t N, int nv, const c
   }
 }
 
-// Pass 2: out[v] = sum over blocks of partial[v][.], in block order.
+// Pass 2: out[v] = sum over tiles of partial[v][.], in tile order.
 __global__ void k_mdot_finish(int nv, int nblk, const cd* __restrict__ partial, cd* __restrict__ out) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= nv) return;
@@ -144,22 +147,43 @@ __global__ void k_mdot_finish(int nv, int nblk, const cd* __restrict__ partial, 
   out[v] = mk<double>(r, i);
 }
 
-// w -= sum_v h[v] V[v]   (or w += when sign = +1); h staged in shared memory.
-__global__ void k_mupdate(int64_t N, int nv, const cd* __restrict__ V, int64_t ldv, const cd* __restrict__ h,
-                          double sign, cd* __restrict__ w) {
-  extern __shared__ cd hs[];
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) hs[v] = h[v];
+// w -= sum_v h[v] V[v], in the basis type; h staged in shared memory.
+template <typename B>
+__global__ void k_mupdate(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv, const cd* __restrict__ h,
+                          C2<B>* __restrict__ w) {
+  extern __shared__ unsigned char hraw[];
+  C2<B>* hs = reinterpret_cast<C2<B>*>(hraw);
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) hs[v] = mk<B>(B(h[v].x), B(h[v].y));
+  __syncthreads();
+  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  B r = 0, i = 0;
+#pragma unroll 4
+  for (int v = 0; v < nv; ++v) {
+    C2<B> a = V[v * ldv + n], c = hs[v];
+    r += c.x * a.x - c.y * a.y;
+    i += c.x * a.y + c.y * a.x;
+  }
+  w[n] = mk<B>(w[n].x - r, w[n].y - i);
+}
+
+// x += d (sum_v y[v] V[v]) in complex double (the solution stays FP64).
+template <typename B>
+__global__ void k_xupdate(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv, const cd* __restrict__ y,
+                          const double* __restrict__ d, cd* __restrict__ x) {
+  extern __shared__ cd ys[];
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) ys[v] = y[v];
   __syncthreads();
   int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (n >= N) return;
   double r = 0, i = 0;
-#pragma unroll 4
   for (int v = 0; v < nv; ++v) {
-    cd a = V[v * ldv + n], c = hs[v];
-    r += c.x * a.x - c.y * a.y;
-    i += c.x * a.y + c.y * a.x;
+    C2<B> a = V[v * ldv + n];
+    cd c = ys[v];
+    r += c.x * double(a.x) - c.y * double(a.y);
+    i += c.x * double(a.y) + c.y * double(a.x);
   }
-  w[n] = mk<double>(w[n].x + sign * r, w[n].y + sign * i);
+  x[n] = mk<double>(x[n].x + d[n] * r, x[n].y + d[n] * i);
 }
 
 // ---------------------------------------------------------------- host loop
@@ -184,59 +208,50 @@ struct Work {
   }
 };
 
-// Shared scratch of the Krylov loops.
+// Shared scratch of the Krylov loop.
 struct Ctx {
   Problem& pr;
   cudaStream_t st;
   int64_t N;
   double* d;        // symmetric scaling
-  cd* u;            // operator scratch
+  cd* u;            // operator input (double)
+  cd* wd;           // operator output (double)
   cd* partial;      // reduction partials
   cd* hdev;         // small device vector
 };
 
 // conj(a) . b over N entries, deterministic; result on the host.
-static pie_status dotc(Ctx& c, int nv, const cd* V, const cd* w, zc* out_host) {
+template <typename B>
+static pie_status dotc(Ctx& c, int nv, const C2<B>* V, const C2<B>* w, zc* out_host) {
   const unsigned tiles = unsigned((c.N + kTile - 1) / kTile);
-  k_mdot<<<dim3(tiles, unsigned(nv)), kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w, c.partial);
+  k_mdot<B><<<dim3(tiles, unsigned(nv)), kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w, c.partial);
   k_mdot_finish<<<nb_(nv, 128), 128, 0, c.st>>>(nv, int(tiles), c.partial, c.hdev);
   pie_status s = cuda_check(cudaMemcpyAsync(out_host, c.hdev, sizeof(cd) * nv, cudaMemcpyDeviceToHost, c.st), "dot");
   if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "dot sync");
   return s;
 }
 
-// out = D Z D in.
-static pie_status scaled_op(Ctx& c, const cd* in, cd* out) {
-  k_scale<<<nb_(c.N, 256), 256, 0, c.st>>>(c.N, c.d, in, c.u);
-  pie_status s = apply_one(c.pr, c.u, out, c.st);
-  if (s != PIE_OK) return s;
-  k_scale<<<nb_(c.N, 256), 256, 0, c.st>>>(c.N, c.d, out, out);
-  return cuda_check(cudaGetLastError(), "gmres launch");
-}
-
-// y += sum_i coef[i] V[i] with host coefficients.
-static pie_status combine(Ctx& c, const cd* V, const std::vector<zc>& coef, int n, cd* y) {
+static pie_status to_dev(Ctx& c, const std::vector<zc>& v, int n) {
   std::vector<cd> h(n);
-  for (int i = 0; i < n; ++i) h[i] = cd{coef[i].real(), coef[i].imag()};
+  for (int i = 0; i < n; ++i) h[i] = cd{v[i].real(), v[i].imag()};
   pie_status s = cuda_check(cudaMemcpyAsync(c.hdev, h.data(), sizeof(cd) * n, cudaMemcpyHostToDevice, c.st), "copy");
-  if (s != PIE_OK) return s;
-  k_mupdate<<<nb_(c.N, 256), 256, sizeof(cd) * n, c.st>>>(c.N, n, V, c.N, c.hdev, 1.0, y);
-  // the host vector must outlive the asynchronous copy
-  return cuda_check(cudaStreamSynchronize(c.st), "combine");
+  if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "copy sync");  // h must outlive the copy
+  return s;
 }
 
-// One GMRES cycle (no restart) on the scaled operator, x0 = 0:
-// V[0] = r / ||r|| given in V; Arnoldi up to m steps or until the rotated
-// residual falls below stop_abs.  On return y (host) holds the coefficients,
-// j the number of steps, and `est` the rotated residual estimate.
 struct Cycle {
   std::vector<zc> H, cs, sn, g, h, h2;
   int m;
   explicit Cycle(int m_) : H(size_t(m_ + 1) * m_), cs(m_), sn(m_), g(m_ + 1), h(m_ + 1), h2(m_ + 1), m(m_) {}
 };
 
-static pie_status arnoldi_cycle(Ctx& c, cd* V, cd* w, Cycle& cy, double beta, double stop_abs, int max_steps,
-                                int& j_out, std::vector<zc>& y, double& est, bool& breakdown, int& steps_done) {
+// One GMRES cycle (no restart) on the scaled operator D Z D, x0 = 0, with
+// V[0] = D r / ||D r|| given: Arnoldi up to m steps or until the rotated
+// residual falls below stop_abs.  On return y (host) holds the coefficients
+// and j the number of steps.
+template <typename B>
+static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, C2<B>* w, Cycle& cy, double beta, double stop_abs, int max_steps,
+                                int& j_out, std::vector<zc>& y, bool& breakdown, int& steps_done) {
   const int64_t N = c.N;
   const int m = cy.m;
   pie_status s = PIE_OK;
@@ -247,21 +262,24 @@ static pie_status arnoldi_cycle(Ctx& c, cd* V, cd* w, Cycle& cy, double beta, do
   breakdown = false;
   zc tmp[1];
   for (; j < m && j < max_steps; ++j) {
-    cd* vj = V + size_t(j) * N;
-    if ((s = scaled_op(c, vj, w)) != PIE_OK) return s;
+    const C2<B>* vj = V + size_t(j) * N;
+    // w = D Z D v_j
+    k_scale<B, double><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, vj, c.u);
+    if ((s = apply_one(c.pr, c.u, c.wd, c.st)) != PIE_OK) return s;
+    k_scale<double, B><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, c.wd, w);
     // classical Gram-Schmidt; a second pass only when the first one cancelled
     // most of w (Daniel-Gragg-Kaufman-Stewart criterion)
-    if ((s = dotc(c, 1, w, w, tmp)) != PIE_OK) return s;
+    if ((s = dotc<B>(c, 1, w, w, tmp)) != PIE_OK) return s;
     const double wn0 = std::sqrt(tmp[0].real());
-    if ((s = dotc(c, j + 1, V, w, cy.h.data())) != PIE_OK) return s;
-    k_mupdate<<<nb_(N, 256), 256, sizeof(cd) * (j + 1), c.st>>>(N, j + 1, V, N, c.hdev, -1.0, w);
-    if ((s = dotc(c, 1, w, w, tmp)) != PIE_OK) return s;
+    if ((s = dotc<B>(c, j + 1, V, w, cy.h.data())) != PIE_OK) return s;
+    k_mupdate<B><<<nb_(N, 256), 256, sizeof(C2<B>) * (j + 1), c.st>>>(N, j + 1, V, N, c.hdev, w);
+    if ((s = dotc<B>(c, 1, w, w, tmp)) != PIE_OK) return s;
     double hn = std::sqrt(tmp[0].real());
     if (hn < 0.7 * wn0) {
-      if ((s = dotc(c, j + 1, V, w, cy.h2.data())) != PIE_OK) return s;
-      k_mupdate<<<nb_(N, 256), 256, sizeof(cd) * (j + 1), c.st>>>(N, j + 1, V, N, c.hdev, -1.0, w);
+      if ((s = dotc<B>(c, j + 1, V, w, cy.h2.data())) != PIE_OK) return s;
+      k_mupdate<B><<<nb_(N, 256), 256, sizeof(C2<B>) * (j + 1), c.st>>>(N, j + 1, V, N, c.hdev, w);
       for (int i = 0; i <= j; ++i) cy.h[i] += cy.h2[i];
-      if ((s = dotc(c, 1, w, w, tmp)) != PIE_OK) return s;
+      if ((s = dotc<B>(c, 1, w, w, tmp)) != PIE_OK) return s;
       hn = std::sqrt(tmp[0].real());
     }
     for (int i = 0; i <= j; ++i)
@@ -289,13 +307,12 @@ static pie_status arnoldi_cycle(Ctx& c, cd* V, cd* w, Cycle& cy, double beta, do
       ++j;
       break;
     }
-    k_axs<<<nb_(N, 256), 256, 0, c.st>>>(N, 1.0 / hn, 0.0, w, V + size_t(j + 1) * N);
+    k_axs<B><<<nb_(N, 256), 256, 0, c.st>>>(N, 1.0 / hn, w, V + size_t(j + 1) * N);
     if (std::abs(cy.g[j + 1]) <= stop_abs) {
       ++j;
       break;
     }
   }
-  est = std::abs(cy.g[j]);
   y.assign(j, zc(0));
   for (int i = j - 1; i >= 0; --i) {
     zc acc = cy.g[i];
@@ -306,27 +323,29 @@ static pie_status arnoldi_cycle(Ctx& c, cd* V, cd* w, Cycle& cy, double beta, do
   return cuda_check(cudaGetLastError(), "arnoldi");
 }
 
-pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, int restart, pie_solve_stats* stats,
-                 cudaStream_t st) {
-  if (pr.io_f32()) {
-    set_error("pie_solve: needs a PIE_FP64 or PIE_MIXED problem (complex double vectors)");
-    return PIE_ERR_PARAM;
-  }
+// Restarted GMRES with the Krylov basis in type B (double for PIE_FP64,
+// float for PIE_MIXED) and the solution, the true residual and the stopping
+// test in complex double: each restart recomputes r = b - Z x in FP64, so
+// the basis precision limits only the progress of a cycle, not the accuracy
+// reached (iterative refinement with a GMRES inner solver).
+template <typename B>
+static pie_status solve_t(Problem& pr, const void* bv, void* xv, double tol, int maxit, int restart,
+                          pie_solve_stats* stats, cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
   const int64_t N = pr.N;
   const int m = std::min(restart, maxit);
   pie_status s = PIE_OK;
   Work wk;
   double* d = wk.get<double>(N, s);
-  cd* V = wk.get<cd>(size_t(N) * (m + 1), s);
-  cd* w = wk.get<cd>(N, s);
+  C2<B>* V = wk.get<C2<B>>(size_t(N) * (m + 1), s);
+  C2<B>* w = wk.get<C2<B>>(N, s);
   cd* u = wk.get<cd>(N, s);
+  cd* wd = wk.get<cd>(N, s);
   cd* r = wk.get<cd>(N, s);
-  cd* t = wk.get<cd>(N, s);
   cd* partial = wk.get<cd>(size_t((N + kTile - 1) / kTile) * (m + 2), s);
   cd* hdev = wk.get<cd>(m + 1, s);
   if (s != PIE_OK) return s;
-  Ctx c{pr, st, N, d, u, partial, hdev};
+  Ctx c{pr, st, N, d, u, wd, partial, hdev};
   const cd* b = static_cast<const cd*>(bv);
   cd* x = static_cast<cd*>(xv);
   const double w2e = pr.w * pr.w * eps0();
@@ -341,7 +360,7 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
   cudaMemsetAsync(x, 0, sizeof(cd) * N, st);
   cudaMemcpyAsync(r, b, sizeof(cd) * N, cudaMemcpyDeviceToDevice, st);
   zc tmp[1];
-  if ((s = dotc(c, 1, b, b, tmp)) != PIE_OK) return s;
+  if ((s = dotc<double>(c, 1, b, b, tmp)) != PIE_OK) return s;
   const double bn = std::sqrt(tmp[0].real());
   int it = 0;
   double rel = bn == 0 ? 0.0 : 1.0;
@@ -349,7 +368,7 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
   Cycle cy(m);
   std::vector<zc> y;
   while (result != PIE_OK && it < maxit) {
-    if ((s = dotc(c, 1, r, r, tmp)) != PIE_OK) return s;
+    if ((s = dotc<double>(c, 1, r, r, tmp)) != PIE_OK) return s;
     rel = std::sqrt(tmp[0].real()) / bn;
     if (!std::isfinite(rel)) {
       set_error("pie_solve: non-finite residual");
@@ -359,30 +378,26 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
       result = PIE_OK;
       break;
     }
-    k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, r, V);  // scaled residual D r
-    if ((s = dotc(c, 1, V, V, tmp)) != PIE_OK) return s;
+    // first Krylov vector: the scaled residual D r, normalised
+    k_scale<double, double><<<nb_(N, 256), 256, 0, st>>>(N, d, r, u);
+    if ((s = dotc<double>(c, 1, u, u, tmp)) != PIE_OK) return s;
     const double beta = std::sqrt(tmp[0].real());
-    k_axs<<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / beta, 0.0, V, V);
+    k_scale<double, B><<<nb_(N, 256), 256, 0, st>>>(N, d, r, V);
+    k_axs<B><<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / beta, V, V);
     int j = 0;
-    double est = 0;
     bool breakdown = false;
-    const double dbn = beta / rel;  // scale of ||D b|| for the inner estimate
-    if ((s = arnoldi_cycle(c, V, w, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, est, breakdown, it)) != PIE_OK)
+    const double dbn = beta / rel;  // scale of ||D b|| for the cycle's stopping estimate
+    if ((s = arnoldi_cycle<B>(c, V, w, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, breakdown, it)) != PIE_OK)
       return s;
-    // x += D (sum_j y_j V_j)
-    cudaMemsetAsync(t, 0, sizeof(cd) * N, st);
-    if ((s = combine(c, V, y, j, t)) != PIE_OK) return s;
-    k_scale<<<nb_(N, 256), 256, 0, st>>>(N, d, t, t);
-    {
-      std::vector<zc> one(1, zc(1.0));
-      if ((s = combine(c, t, one, 1, x)) != PIE_OK) return s;
-    }
-    // true residual r = b - Z x
-    if ((s = apply_one(pr, x, w, st)) != PIE_OK) return s;
-    k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, w, r);
+    // x += D (sum_j y_j V_j), in complex double
+    if ((s = to_dev(c, y, j)) != PIE_OK) return s;
+    k_xupdate<B><<<nb_(N, 256), 256, sizeof(cd) * std::max(j, 1), st>>>(N, j, V, N, hdev, d, x);
+    // true residual r = b - Z x (FP64 vectors)
+    if ((s = apply_one(pr, x, wd, st)) != PIE_OK) return s;
+    k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, wd, r);
     if ((s = cuda_check(cudaGetLastError(), "gmres launch")) != PIE_OK) return s;
     if (breakdown) {
-      if ((s = dotc(c, 1, r, r, tmp)) != PIE_OK) return s;
+      if ((s = dotc<double>(c, 1, r, r, tmp)) != PIE_OK) return s;
       rel = std::sqrt(tmp[0].real()) / bn;
       result = rel <= tol ? PIE_OK : PIE_ERR_BREAKDOWN;
       if (result != PIE_OK) set_error("pie_solve: Arnoldi breakdown before convergence");
@@ -390,7 +405,7 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
     }
   }
   if (result != PIE_OK && result != PIE_ERR_BREAKDOWN) {
-    if ((s = dotc(c, 1, r, r, tmp)) != PIE_OK) return s;
+    if ((s = dotc<double>(c, 1, r, r, tmp)) != PIE_OK) return s;
     rel = std::sqrt(tmp[0].real()) / bn;
     if (rel <= tol)
       result = PIE_OK;
@@ -404,6 +419,16 @@ pie_status solve(Problem& pr, const void* bv, void* xv, double tol, int maxit, i
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return result;
+}
+
+pie_status solve(Problem& pr, const void* b, void* x, double tol, int maxit, int restart, pie_solve_stats* stats,
+                 cudaStream_t st) {
+  if (pr.io_f32()) {
+    set_error("pie_solve: needs a PIE_FP64 or PIE_MIXED problem (complex double vectors)");
+    return PIE_ERR_PARAM;
+  }
+  if (pr.par.precision == PIE_MIXED) return solve_t<float>(pr, b, x, tol, maxit, restart, stats, st);
+  return solve_t<double>(pr, b, x, tol, maxit, restart, stats, st);
 }
 
 }  // namespace pie
