@@ -16,8 +16,9 @@ One MVM y = Z x is, in this order:
 
 Eq. (4) is used with kappa_l = k0 / s_l.  Reading for the scale factors (the
 table of [jp045] is not reproduced in the paper): kappa_l a_l = x is the same at
-every level (s_l = k0 a_l / x), with (tau, x, N_theta) chosen by the error
-search in oracle/search_asd.py.  Reading for the inter-level transfer (the
+every level that is small in wavelengths (s_l = k0 a_l / x), and s_l = 1 (the
+standard diagonalization) once k0 a_l > x, with (tau, x, N_theta) chosen by the
+error search in oracle/search_asd.py.  Reading for the inter-level transfer (the
 paper is silent): patterns on the child's sphere of radius kappa_c are carried
 to the parent's kappa_p by spherical-harmonic analysis to degree N_theta - 1,
 multiplication of degree l by (kappa_p / kappa_c)^l (the small-argument
@@ -71,8 +72,10 @@ class MLFMA:
             raise ValueError("leaf box smaller than 1.5 x the longest triangle edge")
         self.khat, self.wq = angular_grid(ntheta)
         self.P = self.khat.shape[0]
-        self.kappa = {l: x / tr.box_size(l) for l in range(1, L + 1)}
-        self.scale = {l: k0 * tr.box_size(l) / x for l in range(1, L + 1)}
+        # s_l = min(k0 a_l / x, 1): scaled plane waves for boxes small in
+        # wavelengths, the standard diagonalization (s = 1) for larger ones
+        self.kappa = {l: max(x / tr.box_size(l), k0) for l in range(1, L + 1)}
+        self.scale = {l: k0 / self.kappa[l] for l in range(1, L + 1)}
         self._tables()
         self._near()
 

@@ -621,12 +621,12 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st
   for (int l = L - 1; l >= 3 && fft8; --l) {
     k_interp_fft<8, Rf><<<unsigned(pr.lev[l].nb), kFftBatch * kComp * 8, fft_smem<8, Rf>(true), st>>>(
         pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
-        static_cast<const Rf*>(pr.Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l].S));
+        static_cast<const Rf*>(pr.lev[l].Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l].S));
   }
   for (int l = L - 1; l >= 3 && !fft8; --l) {
     k_interp<Rf><<<unsigned(pr.lev[l].nb), tpb, sm, st>>>(
         P, pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
-        static_cast<const Rf*>(pr.Ft), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l].S));
+        static_cast<const Rf*>(pr.lev[l].Ft), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l].S));
   }
   prof_mark(pr, 3, true, st);
   prof_mark(pr, 4, false, st);
@@ -641,12 +641,12 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st
   for (int l = 3; l < L && fft8; ++l) {
     k_anterp_fft<8, Rf><<<unsigned(pr.lev[l].nb), kFftBatch * kComp * 8, fft_smem<8, Rf>(false), st>>>(
         pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
-        static_cast<const Rf*>(pr.Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l + 1].G));
+        static_cast<const Rf*>(pr.lev[l].Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l + 1].G));
   }
   for (int l = 3; l < L && !fft8; ++l) {
     k_anterp<Rf><<<unsigned(pr.lev[l + 1].nb), tpb, sm, st>>>(
         P, pr.lev[l + 1].parent, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
-        static_cast<const Rf*>(pr.F), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l + 1].G));
+        static_cast<const Rf*>(pr.lev[l].F), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l + 1].G));
   }
   prof_mark(pr, 5, true, st);
   prof_mark(pr, 6, false, st);

@@ -32,6 +32,10 @@ struct LevelDev {
   void* S = nullptr;           // [nb][5][P]
   void* G = nullptr;           // [nb][5][P]
   void* phase = nullptr;       // [8][P] interpolation phase for children (l < L)
+  void* F = nullptr;           // [P][P] filter from level l+1 to l (l < L), F[p][p']
+  void* Ft = nullptr;          // [P][P] its transpose
+  void* Kf = nullptr;          // [2 ntheta][ntheta][ntheta] azimuthal blocks of F
+  double kappa = 0;            // kappa_l = k0 / s_l
 };
 
 struct Problem {
@@ -77,9 +81,6 @@ struct Problem {
   void* M = nullptr;             // [T][3][P/2] radiation tables (half grid), triangle-major
   void* PiR = nullptr;           // [P/2][T]    the same tables, sample-major (receiving side)
   void* MR = nullptr;            // [3][P/2][T]
-  void* F = nullptr;             // [P][P]  F[p][p'] (far precision, real)
-  void* Ft = nullptr;            // [P][P]  F[p'][p]
-  void* Kf = nullptr;            // [2 ntheta][ntheta][ntheta] azimuthal blocks of F (real)
   std::vector<LevelDev> lev;     // [L+1]
 
   // per-stage CUDA-event profiling (pie_profile_begin / pie_profile_end)

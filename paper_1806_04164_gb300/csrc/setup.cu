@@ -350,8 +350,9 @@ __global__ void k_trans_table(int P, int tau, double k, double s, double a, cons
   Tt[(int64_t)off * P + p] = mk<Rf>(Rf(-f * ai), Rf(f * ar));
 }
 
-// Degree-rescale filter (same at every level: kappa_l / kappa_{l+1} = 1/2):
-// F[p][q] = sum_{l<ntheta} 2^-l (2l+1)/(4 pi) P_l(khat_p.khat_q) w_q.
+// Degree-rescale filter from level l+1 to level l with ratio
+// r = kappa_l / kappa_{l+1} (1/2 while both levels are scaled, 1 once s = 1):
+// F[p][q] = sum_{n<ntheta} r^n (2n+1)/(4 pi) P_n(khat_p.khat_q) w_q.
 template <typename Rf>
 __global__ void k_filter(int P, int ntheta, double ratio, const double* __restrict__ khat,
                          const double* __restrict__ wgt, Rf* __restrict__ F, Rf* __restrict__ Ft) {
@@ -598,13 +599,17 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
 
   // leaf radiation tables
   const double x = pr.par.kappa_a;
+  // kappa_l = k0 / s_l with s_l = min(k0 a_l / x, 1): boxes small in
+  // wavelengths use the scaled plane waves of Eq. (4), larger ones the
+  // standard diagonalization (s = 1)
+  auto kappa_of = [&](int l) { return std::max(x / tr.box_size(l), pr.k0); };
   pr.Pi = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * (P / 2), s);
   pr.M = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * 3 * (P / 2), s);
   pr.PiR = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * (P / 2), s);
   pr.MR = zalloc(pr, sizeof(C2<Rf>) * size_t(T) * 3 * (P / 2), s);
   if (s != PIE_OK) return s;
   k_rad<Rf><<<unsigned((T * (P / 2) + 255) / 256), 256, 0, st>>>(T, P / 2, pr.vert, pr.cent, pr.area, pr.leaf_of,
-                                                           pr.leaf_center, pr.khat, x / aL, pr.rule7,
+                                                           pr.leaf_center, pr.khat, kappa_of(L), pr.rule7,
                                                            static_cast<C2<Rf>*>(pr.Pi), static_cast<C2<Rf>*>(pr.M),
                                                            static_cast<C2<Rf>*>(pr.PiR), static_cast<C2<Rf>*>(pr.MR));
   if ((s = cuda_check(cudaGetLastError(), "radiation tables")) != PIE_OK) return s;
@@ -639,26 +644,26 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
       lv.trans = zalloc(pr, sizeof(C2<Rf>) * kNoffs * P, s);
       if (s != PIE_OK) return s;
       const double al = tr.box_size(l);
+      lv.kappa = kappa_of(l);
       k_trans_table<Rf><<<unsigned((kNoffs * P + 127) / 128), 128, 0, st>>>(
-          P, pr.par.tau, pr.k0, pr.k0 * al / x, al, pr.khat, pr.wgt, static_cast<C2<Rf>*>(lv.trans));
+          P, pr.par.tau, pr.k0, pr.k0 / lv.kappa, al, pr.khat, pr.wgt, static_cast<C2<Rf>*>(lv.trans));
       if (l < L) {
         lv.phase = zalloc(pr, sizeof(C2<Rf>) * 8 * P, s);
         if (s != PIE_OK) return s;
-        k_phase<Rf><<<unsigned((8 * P + 127) / 128), 128, 0, st>>>(P, x / al, 0.5 * tr.box_size(l + 1), pr.khat,
+        k_phase<Rf><<<unsigned((8 * P + 127) / 128), 128, 0, st>>>(P, lv.kappa, 0.5 * tr.box_size(l + 1), pr.khat,
                                                                    static_cast<C2<Rf>*>(lv.phase));
+        lv.F = zalloc(pr, sizeof(Rf) * P * P, s);
+        lv.Ft = zalloc(pr, sizeof(Rf) * P * P, s);
+        lv.Kf = zalloc(pr, sizeof(Rf) * 2 * nt * nt * nt, s);
+        if (s != PIE_OK) return s;
+        k_filter<Rf><<<unsigned((P * P + 127) / 128), 128, 0, st>>>(P, nt, lv.kappa / kappa_of(l + 1), pr.khat, pr.wgt,
+                                                                    static_cast<Rf*>(lv.F), static_cast<Rf*>(lv.Ft));
+        k_filter_fourier<Rf><<<unsigned((2 * nt * nt * nt + 127) / 128), 128, 0, st>>>(
+            nt, static_cast<const Rf*>(lv.F), static_cast<Rf*>(lv.Kf));
       }
     }
     if (s != PIE_OK) return s;
   }
-  pr.F = zalloc(pr, sizeof(Rf) * P * P, s);
-  pr.Ft = zalloc(pr, sizeof(Rf) * P * P, s);
-  if (s != PIE_OK) return s;
-  k_filter<Rf><<<unsigned((P * P + 127) / 128), 128, 0, st>>>(P, nt, 0.5, pr.khat, pr.wgt, static_cast<Rf*>(pr.F),
-                                                              static_cast<Rf*>(pr.Ft));
-  pr.Kf = zalloc(pr, sizeof(Rf) * 2 * nt * nt * nt, s);
-  if (s != PIE_OK) return s;
-  k_filter_fourier<Rf><<<unsigned((2 * nt * nt * nt + 127) / 128), 128, 0, st>>>(nt, static_cast<const Rf*>(pr.F),
-                                                                                 static_cast<Rf*>(pr.Kf));
   const size_t cio = pr.io_f32() ? sizeof(cf) : sizeof(cd);
   pr.coef = zalloc(pr, cio * 6 * size_t(T), s);
   pr.pot = zalloc(pr, cio * 6 * size_t(T), s);

@@ -91,6 +91,24 @@ def flat_pair(shared: str = "edge"):
     return xyz, tri
 
 
+def square_patch(n: int, side: float = 0.6):
+    """Flat square plate of the given side in the x-y plane, centred at the
+    origin: an n x n grid of squares, each split by its (+x,+y) diagonal into
+    two triangles, normals along +z.  T = 2 n^2, interior edges 3 n^2 - 2 n.
+    Returns (xyz [V,3], tri [T,3])."""
+    g = np.linspace(-0.5 * side, 0.5 * side, n + 1)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1)
+    tri = []
+    for i in range(n):
+        for j in range(n):
+            a = i * (n + 1) + j
+            b = (i + 1) * (n + 1) + j
+            tri.append((a, b, b + 1))
+            tri.append((a, b + 1, a + 1))
+    return xyz, np.array(tri, dtype=np.int32)
+
+
 def complex_normal(shape, seed: int) -> np.ndarray:
     """Complex normal samples, real and imaginary parts each N(0,1), from
     numpy's PCG64 generator with the given seed (complex128)."""

@@ -97,3 +97,19 @@ def test_far_part_reciprocity():
     an = u @ M.apply(v, far=False)
     bn = v @ M.apply(u, far=False)
     assert abs(an - bn) <= 1e-13 * abs(an)
+
+
+@pytest.mark.parametrize("freq", [1e6, 1e8])
+def test_open_patch_both_regimes(freq):
+    """Open surface (boundary edges carry no RWG) at 1 MHz (scaled plane waves,
+    s = 0.04) and 100 MHz (leaf boxes at s = 1, the standard diagonalization):
+    far part within 1e-3 of the dense product per block."""
+    xyz, tri = pi.square_patch(10)
+    k = 2 * np.pi * freq / 299792458.0
+    M = MLFMA(xyz, tri, k, 3)
+    Z = assemble(M.top, k)
+    E = M.top.E
+    for x in (np.r_[pi.complex_normal(E, 1), np.zeros(M.top.T)], np.r_[np.zeros(E), pi.complex_normal(M.top.T, 2)]):
+        yd, ym = Z @ x, M.apply(x)
+        for sl in (slice(0, E), slice(E, None)):
+            assert np.linalg.norm(ym[sl] - yd[sl]) <= 1e-3 * np.linalg.norm(yd[sl])
