@@ -253,6 +253,34 @@ pie_status pie_farfield_adjoint(pie_problem* pr, const double* rhat, int64_t ndi
 pie_status pie_solve(pie_problem* pr, const void* b, void* x, double tol, int maxit, int restart,
                      pie_solve_stats* stats, void* stream);
 
+/* Near-zone fields (Section 2).  The far zone needs J only; near-zone E needs
+ * the charge density rho = i w eps0 n'.A - eps0 n'.grad'Phi, whose second
+ * term solves Eq. (3): int_S (n'.grad'Phi) g = Phi^inc on S (the total scalar
+ * potential vanishes on the conductor).  Eq. (3) is discretised with the
+ * pulses and tested with them, i.e. with the single-layer operator
+ * S_tu = <p_t, g, p_u> -- the pulse-pulse block of Z divided by w^2 eps0 --
+ * which runs through the same near and far stages as Z.
+ * All vectors here are complex double, device, and need a PIE_FP64 or
+ * PIE_MIXED problem; T-vectors are in mesh order.
+ *
+ * pie_apply_single_layer: y = S q (q, y: T complex).
+ * pie_solve_single_layer: GMRES on S q = b, same stopping test, scaling
+ *   (|S_tt|^-1/2) and error codes as pie_solve.
+ * pie_rhs_potential: b_t = <p_t, Phi^inc> for the plane wave of
+ *   pie_rhs_planewave (Phi^inc = -E0 (pol.r) exp(i k0 khat.r)).
+ * pie_nearfield: scattered field E_s(r) = i w mu0 int J g - (1/eps0) int rho
+ *   grad g at npts host points pts (npts x 3, off the surface; the 7-point
+ *   rule per triangle is accurate beyond about one triangle size), from the
+ *   PIE solution x (N) and the charge-density pulse coefficients rho (T).
+ *   E: device npts x 3 complex double. */
+pie_status pie_apply_single_layer(pie_problem* pr, const void* q, void* y, void* stream);
+pie_status pie_solve_single_layer(pie_problem* pr, const void* b, void* x, double tol, int maxit, int restart,
+                                  pie_solve_stats* stats, void* stream);
+pie_status pie_rhs_potential(pie_problem* pr, const double khat[3], const double pol[3], double E0, void* b,
+                             void* stream);
+pie_status pie_nearfield(pie_problem* pr, const void* x, const void* rho, const double* pts, int64_t npts, void* E,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

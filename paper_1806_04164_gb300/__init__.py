@@ -51,7 +51,8 @@ EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_
            "pie_mesh_edges", "pie_problem_create", "pie_problem_destroy", "pie_problem_info", "pie_problem_perm",
            "pie_problem_level", "pie_problem_near", "pie_apply", "pie_apply_near", "pie_problem_stage", "pie_rhs_planewave",
            "pie_farfield", "pie_solve", "pie_profile_begin", "pie_profile_end", "pie_apply_near_noalloc", "pie_apply_t",
-           "pie_farfield_adjoint"]
+           "pie_farfield_adjoint", "pie_apply_single_layer", "pie_solve_single_layer", "pie_rhs_potential",
+           "pie_nearfield"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -84,6 +85,10 @@ def lib():
         L.pie_apply_near_noalloc.argtypes = [vp, vp, vp, i32, vp]
         L.pie_apply_t.argtypes = [vp, vp, vp, i32, i32, i32, vp]
         L.pie_farfield_adjoint.argtypes = [vp, PD, i64, vp, vp, vp]
+        L.pie_apply_single_layer.argtypes = [vp, vp, vp, vp]
+        L.pie_solve_single_layer.argtypes = [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
+        L.pie_rhs_potential.argtypes = [vp, PD, PD, dbl, vp, vp]
+        L.pie_nearfield.argtypes = [vp, vp, vp, PD, i64, vp, vp]
         L.pie_problem_stage.argtypes = [vp, i32, i32, PD, vp]
         L.pie_rhs_planewave.argtypes = [vp, PD, PD, dbl, vp, i32, vp]
         L.pie_farfield.argtypes = [vp, vp, PD, i64, vp, vp]
@@ -247,6 +252,51 @@ class Problem:
                                           ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(u.data_ptr()),
                                           _stream(stream)))
         return u
+
+    def apply_single_layer(self, q, stream=None):
+        """y = S q, S_tu = <p_t, g, p_u> (the operator of Eq. (3))."""
+        import torch
+        q = _dense(q)
+        y = torch.empty_like(q)
+        _check(lib().pie_apply_single_layer(self.handle, ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                            _stream(stream)))
+        return y
+
+    def solve_single_layer(self, b, tol=1e-6, maxit=2000, restart=300, stream=None):
+        """GMRES on S q = b (Eq. (3))."""
+        import torch
+        b = _dense(b)
+        x = torch.zeros_like(b)
+        st = SolveStats()
+        code = lib().pie_solve_single_layer(self.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                            tol, maxit, restart, ctypes.byref(st), _stream(stream))
+        if code not in (0, 8):
+            _check(code)
+        return x, dict(iterations=st.iterations, rel_residual=st.rel_residual, seconds=st.seconds,
+                       converged=code == 0)
+
+    def rhs_potential(self, khat, pol, E0=1.0, stream=None):
+        """b_t = <p_t, Phi^inc> for the plane wave (right-hand side of Eq. (3))."""
+        import torch
+        b = torch.empty(self.T, dtype=torch.complex128, device="cuda")
+        kh = np.ascontiguousarray(khat, np.float64)
+        po = np.ascontiguousarray(pol, np.float64)
+        _check(lib().pie_rhs_potential(self.handle, _ptr(kh, ctypes.c_double), _ptr(po, ctypes.c_double), E0,
+                                       ctypes.c_void_p(b.data_ptr()), _stream(stream)))
+        return b
+
+    def nearfield(self, x, rho, pts, stream=None):
+        """Scattered E at points off the surface from the solution x and the
+        charge-density pulse coefficients rho."""
+        import torch
+        x = _dense(x)
+        rho = _dense(rho)
+        p = np.ascontiguousarray(pts, np.float64)
+        E = torch.empty((p.shape[0], 3), dtype=torch.complex128, device="cuda")
+        _check(lib().pie_nearfield(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
+                                   _ptr(p, ctypes.c_double), p.shape[0], ctypes.c_void_p(E.data_ptr()),
+                                   _stream(stream)))
+        return E
 
     def stage(self, which, level=0, stream=None):
         if which in (0, 1):

@@ -395,4 +395,50 @@ pie_status pie_solve(pie_problem* h, const void* b, void* x, double tol, int max
   return solve(h->p, b, x, tol, maxit, restart, stats, static_cast<cudaStream_t>(stream));
 }
 
+static bool c128_problem(pie_problem* h, const char* who) {
+  if (h->p.io_f32()) {
+    set_error(std::string(who) + ": needs a PIE_FP64 or PIE_MIXED problem (complex double vectors)");
+    return false;
+  }
+  return true;
+}
+
+pie_status pie_apply_single_layer(pie_problem* h, const void* q, void* y, void* stream) {
+  if (!h || !q || !y) {
+    set_error("pie_apply_single_layer: NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  if (!c128_problem(h, "pie_apply_single_layer")) return PIE_ERR_PARAM;
+  return single_layer_one(h->p, q, y, static_cast<cudaStream_t>(stream));
+}
+
+pie_status pie_solve_single_layer(pie_problem* h, const void* b, void* x, double tol, int maxit, int restart,
+                                  pie_solve_stats* stats, void* stream) {
+  if (!h || !b || !x || !(tol > 0) || maxit < 1 || restart < 1) {
+    set_error("pie_solve_single_layer: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  return solve_single_layer(h->p, b, x, tol, maxit, restart, stats, static_cast<cudaStream_t>(stream));
+}
+
+pie_status pie_rhs_potential(pie_problem* h, const double khat[3], const double pol[3], double E0, void* b,
+                             void* stream) {
+  if (!h || !khat || !pol || !b) {
+    set_error("pie_rhs_potential: NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  return rhs_potential(h->p, khat, pol, E0, b, static_cast<cudaStream_t>(stream));
+}
+
+pie_status pie_nearfield(pie_problem* h, const void* x, const void* rho, const double* pts, int64_t npts, void* E,
+                         void* stream) {
+  if (!h || !x || !rho || !pts || !E || npts < 0) {
+    set_error("pie_nearfield: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  if (!c128_problem(h, "pie_nearfield")) return PIE_ERR_PARAM;
+  if (npts == 0) return PIE_OK;
+  return nearzone(h->p, x, rho, pts, npts, E, static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

@@ -992,3 +992,143 @@ pie_status farfield_adjoint(Problem& pr, const double* rhat, int64_t ndir, const
 }
 
 }  // namespace pie
+
+namespace pie {
+
+// ---------------------------------------------------------------- Eq. (3) and near-zone fields
+
+// out = src[off:off+n] * scale
+__global__ void k_slice_scale(int64_t n, const cd* __restrict__ src, double scale, cd* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = mk<double>(scale * src[i].x, scale * src[i].y);
+}
+
+// Single layer of Eq. (3): y_t = <p_t, g, q> for pulse coefficients q
+// (mesh order).  It is the pulse-pulse block of the PIE operator divided by
+// w^2 eps0, applied to [0 ; q] through the same near and far stages.
+pie_status single_layer_one(Problem& pr, const void* q, void* y, cudaStream_t st) {
+  const int64_t E = pr.E, T = pr.T;
+  cd* v = static_cast<cd*>(pr.vec);
+  cd* v2 = static_cast<cd*>(pr.vec2);
+  pie_status s = cuda_check(cudaMemsetAsync(v, 0, sizeof(cd) * E, st), "memset");
+  if (s == PIE_OK) s = cuda_check(cudaMemcpyAsync(v + E, q, sizeof(cd) * T, cudaMemcpyDeviceToDevice, st), "copy");
+  if (s == PIE_OK) s = apply_one(pr, v, v2, st);
+  if (s != PIE_OK) return s;
+  k_slice_scale<<<nblk(T, 256), 256, 0, st>>>(T, v2 + E, 1.0 / (pr.w * pr.w * eps0()), static_cast<cd*>(y));
+  return cuda_check(cudaGetLastError(), "single layer launch");
+}
+
+// b_t = <p_t, Phi^inc> = int_t Phi^inc for the plane-wave potential
+// Phi^inc = -E0 (pol.r) exp(i k khat.r); 7-point rule; b in mesh order.
+__global__ void k_phi_inc(int64_t T, const double* __restrict__ vert, const double* __restrict__ area,
+                          const int64_t* __restrict__ perm, double k0, double kx, double ky, double kz, double ex,
+                          double ey, double ez, double E0, const double* __restrict__ rule, cd* __restrict__ b) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const double* v = vert + 9 * t;
+  double pr_ = 0, pi_ = 0;
+  for (int q = 0; q < 7; ++q) {
+    double r[3];
+    for (int d = 0; d < 3; ++d) r[d] = rule[4 * q] * v[d] + rule[4 * q + 1] * v[3 + d] + rule[4 * q + 2] * v[6 + d];
+    const double wq = rule[4 * q + 3] * area[t];
+    double s, c;
+    sincos(k0 * (kx * r[0] + ky * r[1] + kz * r[2]), &s, &c);
+    const double er = ex * r[0] + ey * r[1] + ez * r[2];
+    pr_ += -wq * E0 * er * c;
+    pi_ += -wq * E0 * er * s;
+  }
+  b[perm[t]] = mk<double>(pr_, pi_);
+}
+
+pie_status rhs_potential(Problem& pr, const double* khat, const double* pol, double E0, void* b, cudaStream_t st) {
+  k_phi_inc<<<nblk(pr.T, 128), 128, 0, st>>>(pr.T, pr.vert, pr.area, pr.perm, pr.k0, khat[0], khat[1], khat[2],
+                                             pol[0], pol[1], pol[2], E0, pr.rule7, static_cast<cd*>(b));
+  return cuda_check(cudaGetLastError(), "rhs potential launch");
+}
+
+// Scattered field at observation points off the surface (Section 2:
+// near-zone E from J and the charge density rho):
+//   E_s(r) = i w mu0 sum_t int_t J g  -  (1/eps0) sum_t rho_t int_t grad_r g,
+// grad_r g = (r - r') (i k - 1/R) g / R; 7-point rule on every triangle (the
+// rule is accurate for points farther than about a triangle size).  One block
+// per point; coef holds the local coefficients of J (tree order), rho the
+// pulse coefficients of the charge density (mesh order).
+template <typename Rio>
+__global__ void k_nearzone(int64_t T, const double* __restrict__ vert, const double* __restrict__ cent,
+                           const double* __restrict__ area, const int64_t* __restrict__ perm,
+                           const C2<Rio>* __restrict__ coef, const cd* __restrict__ rho, const double* __restrict__ pts,
+                           double k0, double wmu, double inv_eps, const double* __restrict__ rule, cd* __restrict__ E) {
+  __shared__ double red[6][32];
+  const int ip = blockIdx.x;
+  const double px = pts[3 * ip], py = pts[3 * ip + 1], pz = pts[3 * ip + 2];
+  double Er[3] = {0, 0, 0}, Ei[3] = {0, 0, 0};
+  for (int64_t t = threadIdx.x; t < T; t += blockDim.x) {
+    const double* v = vert + 9 * t;
+    const C2<Rio>* c = coef + 6 * t;
+    const double ar = double(c[0].x), ai = double(c[0].y);
+    const cd rh = rho[perm[t]];
+    for (int q = 0; q < 7; ++q) {
+      double r[3];
+      for (int d = 0; d < 3; ++d) r[d] = rule[4 * q] * v[d] + rule[4 * q + 1] * v[3 + d] + rule[4 * q + 2] * v[6 + d];
+      const double wq = rule[4 * q + 3] * area[t];
+      const double dx = px - r[0], dy = py - r[1], dz = pz - r[2];
+      const double R = sqrt(dx * dx + dy * dy + dz * dz);
+      double s, cs;
+      sincos(k0 * R, &s, &cs);
+      const double gr = wq * cs / (4.0 * kPi * R), gi = wq * s / (4.0 * kPi * R);
+      // grad g factor: (ik - 1/R)/R * g
+      const double fr = (-gr / R - k0 * gi) / R, fi = (-gi / R + k0 * gr) / R;
+      const double dd[3] = {dx, dy, dz};
+      for (int d = 0; d < 3; ++d) {
+        const double u = r[d] - cent[3 * t + d];
+        const double jr = ar * u + double(c[1 + d].x), ji = ai * u + double(c[1 + d].y);
+        // i w mu0 J g
+        const double agr = jr * gr - ji * gi, agi = jr * gi + ji * gr;
+        Er[d] += -wmu * agi;
+        Ei[d] += wmu * agr;
+        // -(1/eps0) rho grad g
+        const double gdr = fr * dd[d], gdi = fi * dd[d];
+        Er[d] -= inv_eps * (rh.x * gdr - rh.y * gdi);
+        Ei[d] -= inv_eps * (rh.x * gdi + rh.y * gdr);
+      }
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    Er[d] = warp_sum(Er[d]);
+    Ei[d] = warp_sum(Ei[d]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) {
+      red[d][wid] = Er[d];
+      red[3 + d][wid] = Ei[d];
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < int(blockDim.x >> 5); ++w)
+      for (int i = 0; i < 6; ++i) S[i] += red[i][w];
+    for (int d = 0; d < 3; ++d) E[3 * ip + d] = mk<double>(S[d], S[3 + d]);
+  }
+}
+
+pie_status nearzone(Problem& pr, const void* x, const void* rho, const double* pts, int64_t npts, void* E,
+                    cudaStream_t st) {
+  double* d_pts = nullptr;
+  pie_status s = cuda_check(cudaMallocAsync((void**)&d_pts, sizeof(double) * 3 * npts, st), "nearfield alloc");
+  if (s != PIE_OK) return s;
+  s = cuda_check(cudaMemcpyAsync(d_pts, pts, sizeof(double) * 3 * npts, cudaMemcpyHostToDevice, st), "copy");
+  if (s != PIE_OK) return s;
+  const double w2e = pr.w * pr.w * eps0();
+  k_coef<double><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cd*>(x), pr.perm, pr.tri_edge,
+                                                  pr.tri_c, pr.tri_dcp, w2e, static_cast<cd*>(pr.coef), nullptr);
+  k_nearzone<double><<<unsigned(npts), 256, 0, st>>>(pr.T, pr.vert, pr.cent, pr.area, pr.perm,
+                                                     static_cast<const cd*>(pr.coef), static_cast<const cd*>(rho),
+                                                     d_pts, pr.k0, pr.w * kMu0, 1.0 / eps0(), pr.rule7,
+                                                     static_cast<cd*>(E));
+  s = cuda_check(cudaGetLastError(), "nearfield launch");
+  cudaFreeAsync(d_pts, st);
+  return s;
+}
+
+}  // namespace pie

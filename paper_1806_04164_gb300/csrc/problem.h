@@ -91,6 +91,7 @@ struct Problem {
   void* coef = nullptr;          // [T][6] complex (io precision)
   void* coef32 = nullptr;        // [T][6] complex float copy for the MIXED near part
   void* vec = nullptr;           // [N] complex (io precision), adjoint scratch
+  void* vec2 = nullptr;          // [N] complex (io precision), single-layer scratch
   void* pot = nullptr;           // [T][6]
 
   bool near_f32() const { return par.precision != PIE_FP64; }
@@ -111,6 +112,12 @@ pie_status rhs_planewave(Problem& pr, const double* khat, const double* pol, dou
 pie_status farfield(Problem& pr, const void* x, const double* rhat, int64_t ndir, void* E,
                     cudaStream_t st);
 pie_status apply_t_one(Problem& pr, const void* x, void* y, bool conj, cudaStream_t st);
+pie_status single_layer_one(Problem& pr, const void* q, void* y, cudaStream_t st);
+pie_status solve_single_layer(Problem& pr, const void* b, void* x, double tol, int maxit, int restart,
+                              pie_solve_stats* stats, cudaStream_t st);
+pie_status rhs_potential(Problem& pr, const double* khat, const double* pol, double E0, void* b, cudaStream_t st);
+pie_status nearzone(Problem& pr, const void* x, const void* rho, const double* pts, int64_t npts, void* E,
+                    cudaStream_t st);
 pie_status farfield_adjoint(Problem& pr, const double* rhat, int64_t ndir, const void* E, void* u,
                             cudaStream_t st);
 pie_status solve(Problem& pr, const void* b, void* x, double tol, int maxit, int restart,

@@ -669,6 +669,7 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   pr.pot = zalloc(pr, cio * 6 * size_t(T), s);
   if (pr.par.precision == PIE_MIXED) pr.coef32 = zalloc(pr, sizeof(cf) * 6 * size_t(T), s);
   pr.vec = zalloc(pr, cio * size_t(pr.N), s);
+  pr.vec2 = zalloc(pr, cio * size_t(pr.N), s);
   if (s != PIE_OK) return s;
   if ((s = cuda_check(cudaGetLastError(), "setup launch")) != PIE_OK) return s;
   return cuda_check(cudaStreamSynchronize(st), "setup");

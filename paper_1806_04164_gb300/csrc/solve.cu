@@ -82,6 +82,22 @@ __global__ void k_diag_scale(int64_t N, int64_t E, int64_t nnz, const int32_t* _
   dscale[i] = a > 0 ? 1.0 / sqrt(a) : 1.0;
 }
 
+// |S_tt|^{-1/2} for the single layer of Eq. (3) (pulse t in mesh order):
+// S_tt = int_t int_t g, the self-pair moment m0.
+template <typename Rm>
+__global__ void k_diag_single(int64_t T, const int64_t* __restrict__ inv_perm, const int32_t* __restrict__ leaf_of,
+                              const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ near_ptr,
+                              const int32_t* __restrict__ near_idx, const int64_t* __restrict__ row_ptr,
+                              const C2<Rm>* __restrict__ mom, double* __restrict__ dscale) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= T) return;
+  int64_t t = inv_perm[i];
+  int64_t e = near_entry(t, t, leaf_of, leaf_start, near_ptr, near_idx, row_ptr);
+  C2<Rm> m0 = mom[e];
+  double a = sqrt(double(m0.x) * double(m0.x) + double(m0.y) * double(m0.y));
+  dscale[i] = a > 0 ? 1.0 / sqrt(a) : 1.0;
+}
+
 // y = d x, converting between the Krylov basis type and complex double.
 template <typename A, typename B>
 __global__ void k_scale(int64_t N, const double* __restrict__ d, const C2<A>* __restrict__ x, C2<B>* __restrict__ y) {
@@ -212,6 +228,7 @@ struct Work {
 struct Ctx {
   Problem& pr;
   cudaStream_t st;
+  int op;           // 0: the PIE operator Z (N unknowns); 1: the single layer of Eq. (3) (T unknowns)
   int64_t N;
   double* d;        // symmetric scaling
   cd* u;            // operator input (double)
@@ -219,6 +236,11 @@ struct Ctx {
   cd* partial;      // reduction partials
   cd* hdev;         // small device vector
 };
+
+// out = Z in, or out = S in for the single-layer operator of Eq. (3).
+static pie_status op_apply(Ctx& c, const cd* in, cd* out) {
+  return c.op == 0 ? apply_one(c.pr, in, out, c.st) : single_layer_one(c.pr, in, out, c.st);
+}
 
 // conj(a) . b over N entries, deterministic; result on the host.
 template <typename B>
@@ -265,7 +287,7 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, C2<B>* w, Cycle& cy, double be
     const C2<B>* vj = V + size_t(j) * N;
     // w = D Z D v_j
     k_scale<B, double><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, vj, c.u);
-    if ((s = apply_one(c.pr, c.u, c.wd, c.st)) != PIE_OK) return s;
+    if ((s = op_apply(c, c.u, c.wd)) != PIE_OK) return s;
     k_scale<double, B><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, c.wd, w);
     // classical Gram-Schmidt; a second pass only when the first one cancelled
     // most of w (Daniel-Gragg-Kaufman-Stewart criterion)
@@ -329,10 +351,10 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, C2<B>* w, Cycle& cy, double be
 // the basis precision limits only the progress of a cycle, not the accuracy
 // reached (iterative refinement with a GMRES inner solver).
 template <typename B>
-static pie_status solve_t(Problem& pr, const void* bv, void* xv, double tol, int maxit, int restart,
+static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double tol, int maxit, int restart,
                           pie_solve_stats* stats, cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
-  const int64_t N = pr.N;
+  const int64_t N = op == 0 ? pr.N : pr.T;
   const int m = std::min(restart, maxit);
   pie_status s = PIE_OK;
   Work wk;
@@ -345,11 +367,18 @@ static pie_status solve_t(Problem& pr, const void* bv, void* xv, double tol, int
   cd* partial = wk.get<cd>(size_t((N + kTile - 1) / kTile) * (m + 2), s);
   cd* hdev = wk.get<cd>(m + 1, s);
   if (s != PIE_OK) return s;
-  Ctx c{pr, st, N, d, u, wd, partial, hdev};
+  Ctx c{pr, st, op, N, d, u, wd, partial, hdev};
   const cd* b = static_cast<const cd*>(bv);
   cd* x = static_cast<cd*>(xv);
   const double w2e = pr.w * pr.w * eps0();
-  if (pr.near_f32())
+  if (op == 1) {
+    if (pr.near_f32())
+      k_diag_single<float><<<nb_(N, 256), 256, 0, st>>>(N, pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
+                                                        pr.near_idx, pr.row_ptr, static_cast<const cf*>(pr.mom), d);
+    else
+      k_diag_single<double><<<nb_(N, 256), 256, 0, st>>>(N, pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
+                                                         pr.near_idx, pr.row_ptr, static_cast<const cd*>(pr.mom), d);
+  } else if (pr.near_f32())
     k_diag_scale<float><<<nb_(N, 256), 256, 0, st>>>(N, pr.E, pr.nnz, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                      pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx,
                                                      pr.row_ptr, static_cast<const cf*>(pr.mom), w2e, d);
@@ -393,7 +422,7 @@ static pie_status solve_t(Problem& pr, const void* bv, void* xv, double tol, int
     if ((s = to_dev(c, y, j)) != PIE_OK) return s;
     k_xupdate<B><<<nb_(N, 256), 256, sizeof(cd) * std::max(j, 1), st>>>(N, j, V, N, hdev, d, x);
     // true residual r = b - Z x (FP64 vectors)
-    if ((s = apply_one(pr, x, wd, st)) != PIE_OK) return s;
+    if ((s = op_apply(c, x, wd)) != PIE_OK) return s;
     k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, wd, r);
     if ((s = cuda_check(cudaGetLastError(), "gmres launch")) != PIE_OK) return s;
     if (breakdown) {
@@ -427,8 +456,18 @@ pie_status solve(Problem& pr, const void* b, void* x, double tol, int maxit, int
     set_error("pie_solve: needs a PIE_FP64 or PIE_MIXED problem (complex double vectors)");
     return PIE_ERR_PARAM;
   }
-  if (pr.par.precision == PIE_MIXED) return solve_t<float>(pr, b, x, tol, maxit, restart, stats, st);
-  return solve_t<double>(pr, b, x, tol, maxit, restart, stats, st);
+  if (pr.par.precision == PIE_MIXED) return solve_t<float>(pr, 0, b, x, tol, maxit, restart, stats, st);
+  return solve_t<double>(pr, 0, b, x, tol, maxit, restart, stats, st);
+}
+
+pie_status solve_single_layer(Problem& pr, const void* b, void* x, double tol, int maxit, int restart,
+                              pie_solve_stats* stats, cudaStream_t st) {
+  if (pr.io_f32()) {
+    set_error("pie_solve_single_layer: needs a PIE_FP64 or PIE_MIXED problem (complex double vectors)");
+    return PIE_ERR_PARAM;
+  }
+  if (pr.par.precision == PIE_MIXED) return solve_t<float>(pr, 1, b, x, tol, maxit, restart, stats, st);
+  return solve_t<double>(pr, 1, b, x, tol, maxit, restart, stats, st);
 }
 
 }  // namespace pie
