@@ -56,40 +56,43 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
                                               const int32_t* __restrict__ leaf_start,
                                               const int32_t* __restrict__ near_ptr,
                                               const int32_t* __restrict__ near_idx,
+                                              const int32_t* __restrict__ near_off,
                                               const int64_t* __restrict__ row_ptr, const C2<Rm>* __restrict__ mom,
                                               const C2<Rm>* __restrict__ coef, Rm mu0, C2<Rio>* __restrict__ pot) {
   int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (t >= T) return;
-  int b = leaf_of[t];
-  int64_t e = row_ptr[t];
+  const int b = leaf_of[t];
+  const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
+  const int64_t e0 = row_ptr[t];
+  const int len = int(row_ptr[t + 1] - e0);
   C2<Rm> U = mk<Rm>(0, 0), V0 = U, V1 = U, V2 = U, T1 = U, T2 = U;
-  for (int qi = near_ptr[b]; qi < near_ptr[b + 1]; ++qi) {
-    int q = near_idx[qi];
-    int s0 = leaf_start[q];
-    int ns = leaf_start[q + 1] - s0;
-    for (int j = lane; j < ns; j += 32) {
-      int64_t ee = e + j;
-      const C2<Rm>* c = coef + 6 * (int64_t)(s0 + j);
-      C2<Rm> a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
-      C2<Rm> m0 = mom[ee];
-      C2<Rm> mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
-      C2<Rm> ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
-      C2<Rm> mts = mom[7 * nnz + ee];
-      cfma(U, a, mts);
-      cfma(U, b0, mt0);
-      cfma(U, b1, mt1);
-      cfma(U, b2, mt2);
-      cfma(V0, a, ms0);
-      cfma(V0, b0, m0);
-      cfma(V1, a, ms1);
-      cfma(V1, b1, m0);
-      cfma(V2, a, ms2);
-      cfma(V2, b2, m0);
-      cfma(T1, sg, m0);
-      cfma(T2, dd, m0);
-    }
-    e += ns;
+  // the row is the concatenation of the near boxes' source ranges; lanes walk
+  // it flat (32 consecutive entries per step), each lane keeping a cursor on
+  // the near box that holds its position
+  int qi = q0;
+  for (int j = lane; j < len; j += 32) {
+    while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
+    const int64_t s = leaf_start[near_idx[qi]] + (j - near_off[qi]);
+    const int64_t ee = e0 + j;
+    const C2<Rm>* c = coef + 6 * s;
+    C2<Rm> a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
+    C2<Rm> m0 = mom[ee];
+    C2<Rm> mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
+    C2<Rm> ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
+    C2<Rm> mts = mom[7 * nnz + ee];
+    cfma(U, a, mts);
+    cfma(U, b0, mt0);
+    cfma(U, b1, mt1);
+    cfma(U, b2, mt2);
+    cfma(V0, a, ms0);
+    cfma(V0, b0, m0);
+    cfma(V1, a, ms1);
+    cfma(V1, b1, m0);
+    cfma(V2, a, ms2);
+    cfma(V2, b2, m0);
+    cfma(T1, sg, m0);
+    cfma(T2, dd, m0);
   }
   C2<Rm> acc[6] = {U, V0, V1, V2, T1, T2};
 #pragma unroll
@@ -599,7 +602,7 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st
   prof_mark(pr, 0, true, st);
   prof_mark(pr, 1, false, st);
   k_near<Rm, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                        pr.near_idx, pr.row_ptr,
+                                                        pr.near_idx, pr.near_off, pr.row_ptr,
                                                         static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot);
   prof_mark(pr, 1, true, st);
   const int tpb = P < 1024 ? ((P + 31) / 32) * 32 : 1024;
@@ -673,7 +676,7 @@ static pie_status apply_near_t(Problem& pr, const void* xv, void* yv, cudaStream
   k_coef<Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const C2<Rio>*>(xv), pr.perm, pr.tri_edge,
                                                pr.tri_c, pr.tri_dcp, pr.w * pr.w * eps0(), coef, coef32);
   k_near<Rm, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                        pr.near_idx, pr.row_ptr,
+                                                        pr.near_idx, pr.near_off, pr.row_ptr,
                                                         static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot);
   k_assemble<Rio><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                    pr.inv_perm, pot, static_cast<C2<Rio>*>(yv));
@@ -860,7 +863,7 @@ pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, v
     k_coef<float><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cf*>(x), pr.perm, pr.tri_edge,
                                                    pr.tri_c, pr.tri_dcp, w2e, static_cast<cf*>(coef), nullptr);
     k_near<float, float><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                               pr.near_idx, pr.row_ptr, static_cast<const cf*>(pr.mom),
+                                                               pr.near_idx, pr.near_off, pr.row_ptr, static_cast<const cf*>(pr.mom),
                                                                static_cast<const cf*>(coef), float(kMu0),
                                                                static_cast<cf*>(pot));
     k_assemble<float><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
@@ -872,11 +875,11 @@ pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, v
                                                     split ? static_cast<cf*>(coef) : nullptr);
     if (split)
       k_near<float, double><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
-          pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.row_ptr,
+          pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
           static_cast<const cf*>(pr.mom), static_cast<const cf*>(coef), float(kMu0), static_cast<cd*>(pot));
     else
       k_near<double, double><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
-          pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.row_ptr,
+          pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
           static_cast<const cd*>(pr.mom), static_cast<const cd*>(coef), kMu0, static_cast<cd*>(pot));
     k_assemble<double><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                         pr.inv_perm, static_cast<const cd*>(pot), static_cast<cd*>(y));

@@ -67,6 +67,7 @@ struct Problem {
   double* leaf_center = nullptr; // [nleaf*3]
   int32_t* near_ptr = nullptr;   // [nleaf+1]
   int32_t* near_idx = nullptr;
+  int32_t* near_off = nullptr;   // per near-list entry: position of that box's sources in the test rows
   int64_t* row_ptr = nullptr;    // [T+1]
 
   // angular grid

@@ -514,6 +514,14 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   }
   for (size_t i = 0; i < near_ptr.size(); ++i) near_ptr[i] = int32_t(tr.near_ptr[i]);
   for (size_t i = 0; i < near_idx.size(); ++i) near_idx[i] = int32_t(tr.near_idx[i]);
+  std::vector<int32_t> near_off(near_idx.size());
+  for (int64_t b = 0; b < nleaf; ++b) {
+    int32_t acc = 0;
+    for (int64_t qi = tr.near_ptr[b]; qi < tr.near_ptr[b + 1]; ++qi) {
+      near_off[qi] = acc;
+      acc += int32_t(tr.leaf_start[tr.near_idx[qi] + 1] - tr.leaf_start[tr.near_idx[qi]]);
+    }
+  }
   std::vector<int64_t> row_ptr(T + 1, 0);
   for (int64_t i = 0; i < T; ++i) {
     int64_t b = leaf_of[i], cnt = 0;
@@ -582,6 +590,7 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   pr.leaf_center = upload(pr, leaf_center, st, s);
   pr.near_ptr = upload(pr, near_ptr, st, s);
   pr.near_idx = upload(pr, near_idx, st, s);
+  pr.near_off = upload(pr, near_off, st, s);
   pr.row_ptr = upload(pr, row_ptr, st, s);
   pr.khat = upload(pr, khat, st, s);
   pr.wgt = upload(pr, wgt, st, s);
