@@ -185,61 +185,130 @@ __device__ __forceinline__ bool near_singular(const double* ct, const double* cs
   return d2 < __dmul_rn(2.25, fmax(h2t, h2s));
 }
 
-// One warp per test triangle, lanes over its near entries (same order as the
-// product kernel reads them).
-template <typename Rm>
-__global__ void __launch_bounds__(128) k_near_build(int64_t T, int64_t nnz, const int32_t* __restrict__ leaf_of,
-                                                    const int32_t* __restrict__ leaf_start,
-                                                    const int32_t* __restrict__ near_ptr,
-                                                    const int32_t* __restrict__ near_idx,
-                                                    const int64_t* __restrict__ row_ptr,
-                                                    const double* __restrict__ vert, const double* __restrict__ cent,
-                                                    const double* __restrict__ area, const double* __restrict__ h2,
-                                                    double k, const double* __restrict__ rule7,
-                                                    const double* __restrict__ rule64, C2<Rm>* __restrict__ mom) {
+// Near-part set-up in three passes, so that the few expensive near-singular
+// pairs do not stall the warps computing the regular ones:
+//  1. k_count_singular: count the near-singular pairs with t <= s;
+//  2. k_near_regular: regular pairs by the 7 x 7 rule; near-singular pairs
+//     with t <= s are appended to a list;
+//  3. k_near_singular: one thread per listed pair computes the rule in both
+//     orders, averages, and writes the (t,s) and (s,t) entries (mt and ms
+//     swapped), which keeps Z^T = Z.
+// Lanes walk a test row flat, as the product kernel does.
+struct NearGeom {
+  const int32_t* leaf_of;
+  const int32_t* leaf_start;
+  const int32_t* near_ptr;
+  const int32_t* near_idx;
+  const int32_t* near_off;
+  const int64_t* row_ptr;
+  const double* vert;
+  const double* cent;
+  const double* area;
+  const double* h2;
+};
+
+__global__ void __launch_bounds__(256) k_count_singular(int64_t T, NearGeom g, unsigned long long* count) {
   int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (t >= T) return;
-  int b = leaf_of[t];
-  int64_t e = row_ptr[t];
-  const double* vt = vert + 9 * t;
-  const double* ct = cent + 3 * t;
-  for (int qi = near_ptr[b]; qi < near_ptr[b + 1]; ++qi) {
-    int q = near_idx[qi];
-    int s0 = leaf_start[q];
-    int ns = leaf_start[q + 1] - s0;
-    for (int j = lane; j < ns; j += 32) {
-      int64_t s = s0 + j;
-      Moments m;
-      if (near_singular(ct, cent + 3 * s, h2[t], h2[s])) {
-        // the one-sided rule averaged over both orders of the pair, so that
-        // the discrete operator keeps the reciprocity Z^T = Z
-        Moments m2;
-        moments_singular(vt, ct, area[t], vert + 9 * s, cent + 3 * s, area[s], k, rule7, rule64, m);
-        moments_singular(vert + 9 * s, cent + 3 * s, area[s], vt, ct, area[t], k, rule7, rule64, m2);
-        m.m0r = 0.5 * (m.m0r + m2.m0r);
-        m.m0i = 0.5 * (m.m0i + m2.m0i);
-        m.mtsr = 0.5 * (m.mtsr + m2.mtsr);
-        m.mtsi = 0.5 * (m.mtsi + m2.mtsi);
-        for (int d = 0; d < 3; ++d) {
-          double tr = 0.5 * (m.mtr[d] + m2.msr[d]), ti = 0.5 * (m.mti[d] + m2.msi[d]);
-          double sr = 0.5 * (m.msr[d] + m2.mtr[d]), si = 0.5 * (m.msi[d] + m2.mti[d]);
-          m.mtr[d] = tr;
-          m.mti[d] = ti;
-          m.msr[d] = sr;
-          m.msi[d] = si;
-        }
-      } else
-        moments_regular(vt, ct, area[t], vert + 9 * s, cent + 3 * s, area[s], k, rule7, m);
-      int64_t ee = e + j;
-      mom[ee] = mk<Rm>(Rm(m.m0r), Rm(m.m0i));
-      for (int d = 0; d < 3; ++d) {
-        mom[(1 + d) * nnz + ee] = mk<Rm>(Rm(m.mtr[d]), Rm(m.mti[d]));
-        mom[(4 + d) * nnz + ee] = mk<Rm>(Rm(m.msr[d]), Rm(m.msi[d]));
+  const int b = g.leaf_of[t];
+  const int q0 = g.near_ptr[b], q1 = g.near_ptr[b + 1];
+  const int len = int(g.row_ptr[t + 1] - g.row_ptr[t]);
+  int qi = q0;
+  unsigned n = 0;
+  for (int j = lane; j < len; j += 32) {
+    while (qi + 1 < q1 && g.near_off[qi + 1] <= j) ++qi;
+    const int64_t s = g.leaf_start[g.near_idx[qi]] + (j - g.near_off[qi]);
+    if (t <= s && near_singular(g.cent + 3 * t, g.cent + 3 * s, g.h2[t], g.h2[s])) ++n;
+  }
+  n = __reduce_add_sync(0xffffffffu, n);
+  if (lane == 0 && n) atomicAdd(count, (unsigned long long)n);
+}
+
+struct SingPair {
+  int32_t t, s;
+  int64_t e;
+};
+
+template <typename Rm>
+__device__ __forceinline__ void store_moments(C2<Rm>* mom, int64_t nnz, int64_t e, const Moments& m, bool swap) {
+  mom[e] = mk<Rm>(Rm(m.m0r), Rm(m.m0i));
+  for (int d = 0; d < 3; ++d) {
+    const double tr = swap ? m.msr[d] : m.mtr[d], ti = swap ? m.msi[d] : m.mti[d];
+    const double sr = swap ? m.mtr[d] : m.msr[d], si = swap ? m.mti[d] : m.msi[d];
+    mom[(1 + d) * nnz + e] = mk<Rm>(Rm(tr), Rm(ti));
+    mom[(4 + d) * nnz + e] = mk<Rm>(Rm(sr), Rm(si));
+  }
+  mom[7 * nnz + e] = mk<Rm>(Rm(m.mtsr), Rm(m.mtsi));
+}
+
+template <typename Rm>
+__global__ void __launch_bounds__(128) k_near_regular(int64_t T, int64_t nnz, NearGeom g, double k,
+                                                      const double* __restrict__ rule7, C2<Rm>* __restrict__ mom,
+                                                      SingPair* __restrict__ list, unsigned long long* __restrict__ nlist,
+                                                      unsigned long long cap) {
+  int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (t >= T) return;
+  const int b = g.leaf_of[t];
+  const int q0 = g.near_ptr[b], q1 = g.near_ptr[b + 1];
+  const int64_t e0 = g.row_ptr[t];
+  const int len = int(g.row_ptr[t + 1] - e0);
+  const double* vt = g.vert + 9 * t;
+  const double* ct = g.cent + 3 * t;
+  int qi = q0;
+  for (int j = lane; j < len; j += 32) {
+    while (qi + 1 < q1 && g.near_off[qi + 1] <= j) ++qi;
+    const int64_t s = g.leaf_start[g.near_idx[qi]] + (j - g.near_off[qi]);
+    const int64_t e = e0 + j;
+    if (near_singular(ct, g.cent + 3 * s, g.h2[t], g.h2[s])) {
+      if (t <= s) {
+        unsigned long long slot = atomicAdd(nlist, 1ull);
+        if (slot < cap) list[slot] = SingPair{int32_t(t), int32_t(s), e};
       }
-      mom[7 * nnz + ee] = mk<Rm>(Rm(m.mtsr), Rm(m.mtsi));
+      continue;
     }
-    e += ns;
+    Moments m;
+    moments_regular(vt, ct, g.area[t], g.vert + 9 * s, g.cent + 3 * s, g.area[s], k, rule7, m);
+    store_moments(mom, nnz, e, m, false);
+  }
+}
+
+template <typename Rm>
+__global__ void __launch_bounds__(128) k_near_singular(int64_t npairs, int64_t nnz, NearGeom g, double k,
+                                                       const double* __restrict__ rule7,
+                                                       const double* __restrict__ rule64,
+                                                       const SingPair* __restrict__ list, C2<Rm>* __restrict__ mom) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
+  const SingPair pq = list[i];
+  const int64_t t = pq.t, s = pq.s;
+  Moments m, m2;
+  moments_singular(g.vert + 9 * t, g.cent + 3 * t, g.area[t], g.vert + 9 * s, g.cent + 3 * s, g.area[s], k, rule7,
+                   rule64, m);
+  moments_singular(g.vert + 9 * s, g.cent + 3 * s, g.area[s], g.vert + 9 * t, g.cent + 3 * t, g.area[t], k, rule7,
+                   rule64, m2);
+  // two-sided average, as seen from t (test) and s (source)
+  m.m0r = 0.5 * (m.m0r + m2.m0r);
+  m.m0i = 0.5 * (m.m0i + m2.m0i);
+  m.mtsr = 0.5 * (m.mtsr + m2.mtsr);
+  m.mtsi = 0.5 * (m.mtsi + m2.mtsi);
+  for (int d = 0; d < 3; ++d) {
+    const double tr = 0.5 * (m.mtr[d] + m2.msr[d]), ti = 0.5 * (m.mti[d] + m2.msi[d]);
+    const double sr = 0.5 * (m.msr[d] + m2.mtr[d]), si = 0.5 * (m.msi[d] + m2.mti[d]);
+    m.mtr[d] = tr;
+    m.mti[d] = ti;
+    m.msr[d] = sr;
+    m.msi[d] = si;
+  }
+  store_moments(mom, nnz, pq.e, m, false);
+  if (s != t) {
+    // entry (s, t): row s, at the position of t inside the near box of t
+    const int bs = g.leaf_of[s], bt = g.leaf_of[t];
+    int64_t e2 = -1;
+    for (int qi = g.near_ptr[bs]; qi < g.near_ptr[bs + 1]; ++qi)
+      if (g.near_idx[qi] == bt) e2 = g.row_ptr[s] + g.near_off[qi] + (t - g.leaf_start[bt]);
+    if (e2 >= 0) store_moments(mom, nnz, e2, m, true);
   }
 }
 
@@ -598,12 +667,24 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   pr.rule64 = upload(pr, r64, st, s);
   if (s != PIE_OK) return s;
 
-  // near pair moments
+  // near pair moments (three passes, see k_near_regular)
   pr.mom = zalloc(pr, sizeof(C2<Rm>) * kMom * size_t(pr.nnz), s);
+  unsigned long long* dcount = static_cast<unsigned long long*>(zalloc(pr, 2 * sizeof(unsigned long long), s));
   if (s != PIE_OK) return s;
-  k_near_build<Rm><<<unsigned((T * 32 + 127) / 128), 128, 0, st>>>(
-      T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.row_ptr, pr.vert, pr.cent, pr.area, pr.h2,
-      pr.k0, pr.rule7, pr.rule64, static_cast<C2<Rm>*>(pr.mom));
+  NearGeom ng{pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
+              pr.vert, pr.cent, pr.area, pr.h2};
+  cudaMemsetAsync(dcount, 0, 2 * sizeof(unsigned long long), st);
+  k_count_singular<<<unsigned((T * 32 + 255) / 256), 256, 0, st>>>(T, ng, dcount);
+  unsigned long long nsing = 0;
+  if ((s = cuda_check(cudaMemcpyAsync(&nsing, dcount, sizeof(nsing), cudaMemcpyDeviceToHost, st), "count")) != PIE_OK)
+    return s;
+  if ((s = cuda_check(cudaStreamSynchronize(st), "count sync")) != PIE_OK) return s;
+  SingPair* list = static_cast<SingPair*>(zalloc(pr, sizeof(SingPair) * std::max<unsigned long long>(nsing, 1), s));
+  if (s != PIE_OK) return s;
+  k_near_regular<Rm><<<unsigned((T * 32 + 127) / 128), 128, 0, st>>>(
+      T, pr.nnz, ng, pr.k0, pr.rule7, static_cast<C2<Rm>*>(pr.mom), list, dcount + 1, nsing);
+  k_near_singular<Rm><<<unsigned((nsing + 127) / 128), 128, 0, st>>>(int64_t(nsing), pr.nnz, ng, pr.k0, pr.rule7,
+                                                                     pr.rule64, list, static_cast<C2<Rm>*>(pr.mom));
   if ((s = cuda_check(cudaGetLastError(), "near build")) != PIE_OK) return s;
 
   // leaf radiation tables
