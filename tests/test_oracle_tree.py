@@ -75,3 +75,19 @@ def test_leaf_index_formula_and_order():
     lo = tr.x0 + tr.ijk[4][boxes] * a
     c = top.centroid[tr.perm]
     assert np.all(c >= lo - 1e-12) and np.all(c < lo + a + 1e-12)
+
+
+def test_cube_faces_on_box_planes():
+    """Cube faces lie exactly on the root's boundary planes and, with a grid
+    aligned to the boxes, centroids fall on interior planes' sides only through
+    the half-open rule and the clamp; every pair is still partitioned once."""
+    xyz, tri = pi.cube(8)
+    top = build_topology(xyz, tri)
+    tr = build_tree(top.centroid, top.xyz, 4, side=1.0)
+    a = tr.box_size(4)
+    k = tr.leaf_key_of_tri
+    boxes = np.searchsorted(tr.keys[4], k)
+    lo = tr.x0 + tr.ijk[4][boxes] * a
+    c = top.centroid[tr.perm]
+    inside = (c >= lo) & ((c < lo + a) | (np.isclose(c, 0.5) & np.isclose(lo + a, 0.5)))
+    assert np.all(inside)
