@@ -82,6 +82,9 @@ typedef struct {
   int ntheta;        /* angular samples: ntheta (even) Gauss-Legendre nodes
                         in cos(theta) x 2 ntheta azimuths, P = 2 ntheta^2 */
   int precision;     /* pie_precision */
+  int max_nrhs;      /* right-hand sides one pass of pie_apply handles (the
+                        near part reads each pair's moments once for up to 8
+                        of them); work buffers scale with it */
 } pie_params;
 
 typedef struct {
@@ -103,7 +106,7 @@ typedef struct {
 const char* pie_last_error(void);
 
 /* Default parameters: levels 3, root_side 0, tau 7, kappa_a 0.08, ntheta 8,
- * precision PIE_FP64: product error below 1e-3 with an FP64 rounding
+ * precision PIE_FP64, max_nrhs 1: product error below 1e-3 with an FP64 rounding
  * nonlinearity (~2.5e-6) low enough for GMRES to reach 1e-6 (the error and
  * rounding trade-off of Eqs. (4)-(5)). */
 void pie_params_default(pie_params* p);
@@ -150,7 +153,7 @@ pie_status pie_problem_near(const pie_problem* pr, int64_t* nlist, int64_t* ptr,
 
 /* y = Z x (Section 3: one MVM).  x, y: device buffers of N x nrhs complex
  * numbers, column-major (column j at offset j*N), caller-owned, not
- * overlapping.  dtype must be PIE_C128 for PIE_FP64 / PIE_MIXED problems and
+ * overlapping; right-hand sides run in batches of max_nrhs.  dtype must be PIE_C128 for PIE_FP64 / PIE_MIXED problems and
  * PIE_C64 for PIE_FP32.  Asynchronous on the stream.  Errors: PIE_ERR_PARAM,
  * PIE_ERR_CUDA. */
 pie_status pie_apply(pie_problem* pr, const void* x, void* y, int nrhs, int dtype, void* stream);

@@ -33,7 +33,8 @@ class PieError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("root_side", ctypes.c_double), ("tau", ctypes.c_int),
-                ("kappa_a", ctypes.c_double), ("ntheta", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("kappa_a", ctypes.c_double), ("ntheta", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_nrhs", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -154,11 +155,11 @@ class Problem:
     """PIE operator for one mesh and wavenumber (pie_problem_create)."""
 
     def __init__(self, mesh, k0, levels, root_side=0.0, tau=DEFAULT_TAU, kappa_a=DEFAULT_KAPPA_A,
-                 ntheta=DEFAULT_NTHETA, precision=PIE_FP64, stream=None):
+                 ntheta=DEFAULT_NTHETA, precision=PIE_FP64, max_nrhs=1, stream=None):
         self.mesh = mesh
         self.k0 = float(k0)
         self.precision = precision
-        p = Params(levels, root_side, tau, kappa_a, ntheta, precision)
+        p = Params(levels, root_side, tau, kappa_a, ntheta, precision, max_nrhs)
         h = ctypes.c_void_p()
         _check(lib().pie_problem_create(mesh.handle, self.k0, ctypes.byref(p), _stream(stream), ctypes.byref(h)))
         self.handle = h

@@ -33,6 +33,7 @@ void pie_params_default(pie_params* p) {
   p->kappa_a = 0.08;
   p->ntheta = 8;
   p->precision = PIE_FP64;
+  p->max_nrhs = 1;
 }
 
 pie_status pie_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, pie_mesh** out) {
@@ -97,7 +98,7 @@ pie_status pie_problem_create(const pie_mesh* m, double k0, const pie_params* pa
   *out = nullptr;
   if (!(k0 > 0) || par->levels < 3 || par->levels > 21 || par->tau < 0 || par->tau > 30 || par->ntheta < 1 ||
       2 * par->ntheta * par->ntheta > 1024 || (par->ntheta & 1) || !(par->kappa_a > 0) || par->precision < 0 ||
-      par->precision > 2) {
+      par->precision > 2 || par->max_nrhs < 1 || par->max_nrhs > 1024) {
     set_error("pie_problem_create: parameter out of range");
     return PIE_ERR_PARAM;
   }
@@ -224,10 +225,19 @@ static pie_status apply_cols(pie_problem* h, const void* x, void* y, int nrhs, i
   }
   size_t es = pr.io_f32() ? sizeof(cf) : sizeof(cd);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  for (int j = 0; j < nrhs; ++j) {
-    const char* xj = static_cast<const char*>(x) + es * size_t(pr.N) * j;
-    char* yj = static_cast<char*>(y) + es * size_t(pr.N) * j;
-    pie_status s = near ? apply_near_one(pr, xj, yj, st) : apply_one(pr, xj, yj, st);
+  if (near) {
+    for (int j = 0; j < nrhs; ++j) {
+      pie_status s = apply_near_one(pr, static_cast<const char*>(x) + es * size_t(pr.N) * j,
+                                    static_cast<char*>(y) + es * size_t(pr.N) * j, st);
+      if (s != PIE_OK) return s;
+    }
+    return PIE_OK;
+  }
+  // batches of up to max_nrhs right-hand sides share each pass over the operator
+  for (int j = 0; j < nrhs; j += pr.par.max_nrhs) {
+    const int nb = std::min(pr.par.max_nrhs, nrhs - j);
+    pie_status s = apply_batch(pr, static_cast<const char*>(x) + es * size_t(pr.N) * j,
+                               static_cast<char*>(y) + es * size_t(pr.N) * j, nb, st);
     if (s != PIE_OK) return s;
   }
   return PIE_OK;

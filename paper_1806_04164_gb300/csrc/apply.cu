@@ -3,6 +3,7 @@
 // translation (Eq. (5) operators), anterpolation, leaf disaggregation and
 // Galerkin assembly (Section 2).
 #include <cstdio>
+#include <type_traits>
 
 #include "device.cuh"
 
@@ -14,9 +15,13 @@ template <typename Rio>
 __global__ void k_coef(int64_t T, int64_t E, const C2<Rio>* __restrict__ x, const int64_t* __restrict__ perm,
                        const int32_t* __restrict__ tri_edge, const double* __restrict__ tri_c,
                        const double* __restrict__ tri_dcp, double w2e, C2<Rio>* __restrict__ coef,
-                       cf* __restrict__ coef32) {
+                       cf* __restrict__ coef32, int64_t sx = 0, int64_t sc = 0) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= T) return;
+  // right-hand side blockIdx.y (strides sx, sc between right-hand sides)
+  x += blockIdx.y * sx;
+  if (coef) coef += blockIdx.y * sc;
+  if (coef32) coef32 += blockIdx.y * sc;
   double ar = 0, ai = 0, br[3] = {0, 0, 0}, bi[3] = {0, 0, 0};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -51,22 +56,29 @@ __global__ void k_coef(int64_t T, int64_t E, const C2<Rio>* __restrict__ x, cons
 // eight pair moments are stored plane by plane ([8][nnz]), so a warp reads
 // 32 consecutive entries of each plane (measured faster than per-pair
 // records with vector loads).  Writes pot[t] (initialises it).
-template <typename Rm, typename Rio>
+template <typename Rm, typename Rio, int RB = 1>
 __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int32_t* __restrict__ leaf_of,
                                               const int32_t* __restrict__ leaf_start,
                                               const int32_t* __restrict__ near_ptr,
                                               const int32_t* __restrict__ near_idx,
                                               const int32_t* __restrict__ near_off,
                                               const int64_t* __restrict__ row_ptr, const C2<Rm>* __restrict__ mom,
-                                              const C2<Rm>* __restrict__ coef, Rm mu0, C2<Rio>* __restrict__ pot) {
+                                              const C2<Rm>* __restrict__ coef, Rm mu0, C2<Rio>* __restrict__ pot,
+                                              int nrhs = 1, int64_t sc = 0, int64_t sp = 0) {
   int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (t >= T) return;
+  // right-hand sides r0 .. r0 + RB - 1 share every moment load
+  const int r0 = blockIdx.y * RB;
   const int b = leaf_of[t];
   const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
   const int64_t e0 = row_ptr[t];
   const int len = int(row_ptr[t + 1] - e0);
-  C2<Rm> U = mk<Rm>(0, 0), V0 = U, V1 = U, V2 = U, T1 = U, T2 = U;
+  C2<Rm> acc[RB][6];
+#pragma unroll
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[r][i] = mk<Rm>(0, 0);
   // the row is the concatenation of the near boxes' source ranges; lanes walk
   // it flat (32 consecutive entries per step), each lane keeping a cursor on
   // the near box that holds its position
@@ -75,37 +87,44 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
     while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
     const int64_t s = leaf_start[near_idx[qi]] + (j - near_off[qi]);
     const int64_t ee = e0 + j;
-    const C2<Rm>* c = coef + 6 * s;
-    C2<Rm> a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
     C2<Rm> m0 = mom[ee];
     C2<Rm> mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
     C2<Rm> ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
     C2<Rm> mts = mom[7 * nnz + ee];
-    cfma(U, a, mts);
-    cfma(U, b0, mt0);
-    cfma(U, b1, mt1);
-    cfma(U, b2, mt2);
-    cfma(V0, a, ms0);
-    cfma(V0, b0, m0);
-    cfma(V1, a, ms1);
-    cfma(V1, b1, m0);
-    cfma(V2, a, ms2);
-    cfma(V2, b2, m0);
-    cfma(T1, sg, m0);
-    cfma(T2, dd, m0);
-  }
-  C2<Rm> acc[6] = {U, V0, V1, V2, T1, T2};
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    acc[i].x = warp_sum(acc[i].x);
-    acc[i].y = warp_sum(acc[i].y);
+    for (int r = 0; r < RB; ++r) {
+      if (r0 + r >= nrhs) break;
+      const C2<Rm>* c = coef + (r0 + r) * sc + 6 * s;
+      C2<Rm> a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
+      cfma(acc[r][0], a, mts);
+      cfma(acc[r][0], b0, mt0);
+      cfma(acc[r][0], b1, mt1);
+      cfma(acc[r][0], b2, mt2);
+      cfma(acc[r][1], a, ms0);
+      cfma(acc[r][1], b0, m0);
+      cfma(acc[r][2], a, ms1);
+      cfma(acc[r][2], b1, m0);
+      cfma(acc[r][3], a, ms2);
+      cfma(acc[r][3], b2, m0);
+      cfma(acc[r][4], sg, m0);
+      cfma(acc[r][5], dd, m0);
+    }
   }
-  if (lane == 0) {
-    C2<Rio>* o = pot + 6 * t;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) o[i] = mk<Rio>(Rio(mu0 * acc[i].x), Rio(mu0 * acc[i].y));
-    o[4] = cvt<Rio>(acc[4]);
-    o[5] = cvt<Rio>(acc[5]);
+  for (int r = 0; r < RB; ++r) {
+    if (r0 + r >= nrhs) break;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      acc[r][i].x = warp_sum(acc[r][i].x);
+      acc[r][i].y = warp_sum(acc[r][i].y);
+    }
+    if (lane == 0) {
+      C2<Rio>* o = pot + (r0 + r) * sp + 6 * t;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) o[i] = mk<Rio>(Rio(mu0 * acc[r][i].x), Rio(mu0 * acc[r][i].y));
+      o[4] = cvt<Rio>(acc[r][4]);
+      o[5] = cvt<Rio>(acc[r][5]);
+    }
   }
 }
 
@@ -125,8 +144,10 @@ __device__ __forceinline__ int antipode(int q, int ntheta) {
 template <typename Rf>
 __global__ void k_agg(int P, int ntheta, const int32_t* __restrict__ leaf_start, const C2<Rf>* __restrict__ Pi,
                       const C2<Rf>* __restrict__ M, const C2<Rf>* __restrict__ coef, Rf mu0,
-                      C2<Rf>* __restrict__ S) {
+                      C2<Rf>* __restrict__ S, int64_t sc = 0, int64_t sS = 0) {
   const int b = blockIdx.x;
+  coef += blockIdx.y * sc;
+  S += blockIdx.y * sS;
   const int Ph = P / 2;
   const int t0 = leaf_start[b], t1 = leaf_start[b + 1];
   for (int q = threadIdx.x; q < Ph; q += blockDim.x) {
@@ -168,7 +189,9 @@ __global__ void k_agg(int P, int ntheta, const int32_t* __restrict__ leaf_start,
 template <typename Rf>
 __global__ void k_interp(int P, const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child,
                          const C2<Rf>* __restrict__ Sc, const Rf* __restrict__ Ft, const C2<Rf>* __restrict__ phase,
-                         C2<Rf>* __restrict__ Sp) {
+                         C2<Rf>* __restrict__ Sp, int64_t sSc = 0, int64_t sSp = 0) {
+  Sc += blockIdx.y * sSc;
+  Sp += blockIdx.y * sSp;
   extern __shared__ unsigned char smem_raw[];
   C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw);
   int b = blockIdx.x;
@@ -252,7 +275,10 @@ constexpr int kFftBatch = 4;  // children per batch in the factorised filter ker
 template <int NT, typename Rf>
 __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
     const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Sc,
-    const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Sp) {
+    const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Sp, int64_t sSc = 0,
+    int64_t sSp = 0) {
+  Sc += blockIdx.y * sSc;
+  Sp += blockIdx.y * sSp;
   constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch;
   // rows padded by one element (AP, BP) so that lanes striding over rows hit
   // distinct shared-memory banks
@@ -336,7 +362,10 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
 template <int NT, typename Rf>
 __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
     const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Gp,
-    const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Gc) {
+    const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Gc, int64_t sGp = 0,
+    int64_t sGc = 0) {
+  Gp += blockIdx.y * sGp;
+  Gc += blockIdx.y * sGc;
   constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch;
   constexpr int AP = NT + 1, BP = NPHI + 1;  // padded rows (bank spreading)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -409,8 +438,10 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
 template <typename Rf>
 __global__ void k_trans(int P, const int32_t* __restrict__ il_ptr, const int32_t* __restrict__ il_idx,
                         const int32_t* __restrict__ il_off, const C2<Rf>* __restrict__ Tt,
-                        const C2<Rf>* __restrict__ S, C2<Rf>* __restrict__ G) {
+                        const C2<Rf>* __restrict__ S, C2<Rf>* __restrict__ G, int64_t sS = 0) {
   int d = blockIdx.x;
+  S += blockIdx.y * sS;
+  G += blockIdx.y * sS;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     C2<Rf> acc[kComp];
 #pragma unroll
@@ -432,7 +463,9 @@ __global__ void k_trans(int P, const int32_t* __restrict__ il_ptr, const int32_t
 template <typename Rf>
 __global__ void k_anterp(int P, const int32_t* __restrict__ parent, const int8_t* __restrict__ oct_child,
                          const C2<Rf>* __restrict__ Gp, const Rf* __restrict__ F, const C2<Rf>* __restrict__ phase,
-                         C2<Rf>* __restrict__ Gc) {
+                         C2<Rf>* __restrict__ Gc, int64_t sGp = 0, int64_t sGc = 0) {
+  Gp += blockIdx.y * sGp;
+  Gc += blockIdx.y * sGc;
   extern __shared__ unsigned char smem_raw[];
   C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw);
   int ch = blockIdx.x;
@@ -476,9 +509,12 @@ __global__ void k_anterp(int P, const int32_t* __restrict__ parent, const int8_t
 template <typename Rf, typename Rio>
 __global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, int ntheta, const int32_t* __restrict__ leaf_of,
                                                 const C2<Rf>* __restrict__ PiR, const C2<Rf>* __restrict__ MR,
-                                                const C2<Rf>* __restrict__ G, C2<Rio>* __restrict__ pot) {
+                                                const C2<Rf>* __restrict__ G, C2<Rio>* __restrict__ pot,
+                                                int64_t sG = 0, int64_t sp = 0) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= T) return;
+  G += blockIdx.y * sG;
+  pot += blockIdx.y * sp;
   const int Ph = P / 2;
   const C2<Rf>* g = G + (int64_t)leaf_of[t] * kComp * P;
   C2<Rf> acc[6];
@@ -527,9 +563,11 @@ template <typename Rio>
 __global__ void k_assemble(int64_t N, int64_t E, const int32_t* __restrict__ edge_tt,
                            const int8_t* __restrict__ edge_k, const double* __restrict__ tri_c,
                            const double* __restrict__ tri_dcp, const int64_t* __restrict__ inv_perm,
-                           const C2<Rio>* __restrict__ pot, C2<Rio>* __restrict__ y) {
+                           const C2<Rio>* __restrict__ pot, C2<Rio>* __restrict__ y, int64_t sp = 0, int64_t sy = 0) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
+  pot += blockIdx.y * sp;
+  y += blockIdx.y * sy;
   if (i < E) {
     double yr = 0, yi = 0;
 #pragma unroll
@@ -585,7 +623,7 @@ static pie_status fft_prepare() {
 }
 
 template <typename Rm, typename Rf, typename Rio>
-static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st) {
+static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaStream_t st) {
   const int P = pr.P;
   const int L = pr.tree.L;
   const C2<Rio>* x = static_cast<const C2<Rio>*>(xv);
@@ -593,26 +631,42 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st
   C2<Rio>* coef = static_cast<C2<Rio>*>(pr.coef);
   C2<Rio>* pot = static_cast<C2<Rio>*>(pr.pot);
   const double w2e = pr.w * pr.w * eps0();
+  const unsigned nr = unsigned(nrhs);
+  const int64_t sN = pr.N, sT = 6 * pr.T;  // right-hand-side strides of x / y and of coef / pot
   constexpr bool split = sizeof(Rm) < sizeof(Rio);  // float near part, double coefficients
   cf* coef32 = split ? static_cast<cf*>(pr.coef32) : nullptr;
   const C2<Rm>* ncoef = split ? reinterpret_cast<const C2<Rm>*>(coef32) : reinterpret_cast<const C2<Rm>*>(coef);
   prof_mark(pr, 0, false, st);
-  k_coef<Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, x, pr.perm, pr.tri_edge, pr.tri_c, pr.tri_dcp, w2e,
-                                               coef, coef32);
+  k_coef<Rio><<<dim3(nblk(pr.T, 256), nr), 256, 0, st>>>(pr.T, pr.E, x, pr.perm, pr.tri_edge, pr.tri_c, pr.tri_dcp,
+                                                         w2e, coef, coef32, sN, sT);
   prof_mark(pr, 0, true, st);
   prof_mark(pr, 1, false, st);
-  k_near<Rm, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                        pr.near_idx, pr.near_off, pr.row_ptr,
-                                                        static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot);
+  // the near part reads each pair's moments once for RB right-hand sides
+  // (RB chosen per call: a wide accumulator set costs occupancy when unused)
+  auto near_launch = [&](auto rb) {
+    constexpr int RB = decltype(rb)::value;
+    k_near<Rm, Rio, RB><<<dim3(nblk(pr.T * 32, 256), unsigned((nrhs + RB - 1) / RB)), 256, 0, st>>>(
+        pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
+        static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot, nrhs, sT, sT);
+  };
+  if (nrhs == 1)
+    near_launch(std::integral_constant<int, 1>());
+  else if (nrhs == 2 || sizeof(Rm) == 8)
+    near_launch(std::integral_constant<int, 2>());
+  else if (nrhs <= 4)
+    near_launch(std::integral_constant<int, 4>());
+  else
+    near_launch(std::integral_constant<int, 8>());
   prof_mark(pr, 1, true, st);
   const int tpb = P < 1024 ? ((P + 31) / 32) * 32 : 1024;
   const C2<Rf>* Pi = static_cast<const C2<Rf>*>(pr.Pi);
   const C2<Rf>* M = static_cast<const C2<Rf>*>(pr.M);
+  auto sl = [&](int l) { return int64_t(pr.lev[l].nb) * kComp * P; };  // pattern stride per right-hand side
   prof_mark(pr, 2, false, st);
   // far coefficients in the far precision (MIXED and FP64: the io buffer)
-  const C2<Rf>* fcoef = reinterpret_cast<const C2<Rf>*>(sizeof(Rf) == sizeof(Rio) ? (const void*)coef : pr.coef32);
-  k_agg<Rf><<<unsigned(pr.lev[L].nb), ((P / 2 + 31) / 32) * 32, 0, st>>>(P, pr.par.ntheta, pr.leaf_start, Pi, M, fcoef,
-                                                                       Rf(kMu0), static_cast<C2<Rf>*>(pr.lev[L].S));
+  const C2<Rf>* fcoef = reinterpret_cast<const C2<Rf>*>(coef);
+  k_agg<Rf><<<dim3(unsigned(pr.lev[L].nb), nr), ((P / 2 + 31) / 32) * 32, 0, st>>>(
+      P, pr.par.ntheta, pr.leaf_start, Pi, M, fcoef, Rf(kMu0), static_cast<C2<Rf>*>(pr.lev[L].S), sT, sl(L));
   prof_mark(pr, 2, true, st);
   const size_t sm = sizeof(C2<Rf>) * kComp * P;
   const bool fft8 = pr.par.ntheta == 8;
@@ -622,44 +676,47 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, cudaStream_t st
   }
   prof_mark(pr, 3, false, st);
   for (int l = L - 1; l >= 3 && fft8; --l) {
-    k_interp_fft<8, Rf><<<unsigned(pr.lev[l].nb), kFftBatch * kComp * 8, fft_smem<8, Rf>(true), st>>>(
+    k_interp_fft<8, Rf><<<dim3(unsigned(pr.lev[l].nb), nr), kFftBatch * kComp * 8, fft_smem<8, Rf>(true), st>>>(
         pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
-        static_cast<const Rf*>(pr.lev[l].Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l].S));
+        static_cast<const Rf*>(pr.lev[l].Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase),
+        static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l));
   }
   for (int l = L - 1; l >= 3 && !fft8; --l) {
-    k_interp<Rf><<<unsigned(pr.lev[l].nb), tpb, sm, st>>>(
+    k_interp<Rf><<<dim3(unsigned(pr.lev[l].nb), nr), tpb, sm, st>>>(
         P, pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
-        static_cast<const Rf*>(pr.lev[l].Ft), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l].S));
+        static_cast<const Rf*>(pr.lev[l].Ft), static_cast<const C2<Rf>*>(pr.lev[l].phase),
+        static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l));
   }
   prof_mark(pr, 3, true, st);
   prof_mark(pr, 4, false, st);
   for (int l = 3; l <= L; ++l) {
-    k_trans<Rf><<<unsigned(pr.lev[l].nb), tpb, 0, st>>>(P, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off,
-                                                        static_cast<const C2<Rf>*>(pr.lev[l].trans),
-                                                        static_cast<const C2<Rf>*>(pr.lev[l].S),
-                                                        static_cast<C2<Rf>*>(pr.lev[l].G));
+    k_trans<Rf><<<dim3(unsigned(pr.lev[l].nb), nr), tpb, 0, st>>>(
+        P, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off, static_cast<const C2<Rf>*>(pr.lev[l].trans),
+        static_cast<const C2<Rf>*>(pr.lev[l].S), static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
   }
   prof_mark(pr, 4, true, st);
   prof_mark(pr, 5, false, st);
   for (int l = 3; l < L && fft8; ++l) {
-    k_anterp_fft<8, Rf><<<unsigned(pr.lev[l].nb), kFftBatch * kComp * 8, fft_smem<8, Rf>(false), st>>>(
+    k_anterp_fft<8, Rf><<<dim3(unsigned(pr.lev[l].nb), nr), kFftBatch * kComp * 8, fft_smem<8, Rf>(false), st>>>(
         pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
-        static_cast<const Rf*>(pr.lev[l].Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l + 1].G));
+        static_cast<const Rf*>(pr.lev[l].Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase),
+        static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1));
   }
   for (int l = 3; l < L && !fft8; ++l) {
-    k_anterp<Rf><<<unsigned(pr.lev[l + 1].nb), tpb, sm, st>>>(
+    k_anterp<Rf><<<dim3(unsigned(pr.lev[l + 1].nb), nr), tpb, sm, st>>>(
         P, pr.lev[l + 1].parent, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
-        static_cast<const Rf*>(pr.lev[l].F), static_cast<const C2<Rf>*>(pr.lev[l].phase), static_cast<C2<Rf>*>(pr.lev[l + 1].G));
+        static_cast<const Rf*>(pr.lev[l].F), static_cast<const C2<Rf>*>(pr.lev[l].phase),
+        static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1));
   }
   prof_mark(pr, 5, true, st);
   prof_mark(pr, 6, false, st);
-  k_disagg<Rf, Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, P, pr.par.ntheta, pr.leaf_of,
-                                                    static_cast<const C2<Rf>*>(pr.PiR), static_cast<const C2<Rf>*>(pr.MR),
-                                                    static_cast<const C2<Rf>*>(pr.lev[L].G), pot);
+  k_disagg<Rf, Rio><<<dim3(nblk(pr.T, 256), nr), 256, 0, st>>>(
+      pr.T, P, pr.par.ntheta, pr.leaf_of, static_cast<const C2<Rf>*>(pr.PiR), static_cast<const C2<Rf>*>(pr.MR),
+      static_cast<const C2<Rf>*>(pr.lev[L].G), pot, sl(L), sT);
   prof_mark(pr, 6, true, st);
   prof_mark(pr, 7, false, st);
-  k_assemble<Rio><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
-                                                   pr.inv_perm, pot, y);
+  k_assemble<Rio><<<dim3(nblk(pr.N, 256), nr), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c,
+                                                             pr.tri_dcp, pr.inv_perm, pot, y, sT, sN);
   prof_mark(pr, 7, true, st);
   if (pr.prof_n < pr.prof_cap) ++pr.prof_n;
   return cuda_check(cudaGetLastError(), "apply launch");
@@ -694,18 +751,24 @@ pie_status apply_near_one(Problem& pr, const void* x, void* y, cudaStream_t st) 
   }
 }
 
-pie_status apply_one(Problem& pr, const void* x, void* y, cudaStream_t st) {
+pie_status apply_batch(Problem& pr, const void* x, void* y, int nrhs, cudaStream_t st) {
+  if (nrhs < 1 || nrhs > pr.par.max_nrhs) {
+    set_error("batch larger than max_nrhs");
+    return PIE_ERR_PARAM;
+  }
   switch (pr.par.precision) {
     case PIE_FP64:
-      return apply_t<double, double, double>(pr, x, y, st);
+      return apply_t<double, double, double>(pr, x, y, nrhs, st);
     case PIE_FP32:
-      return apply_t<float, float, float>(pr, x, y, st);
+      return apply_t<float, float, float>(pr, x, y, nrhs, st);
     case PIE_MIXED:
-      return apply_t<float, double, double>(pr, x, y, st);
+      return apply_t<float, double, double>(pr, x, y, nrhs, st);
   }
   set_error("unknown precision");
   return PIE_ERR_PARAM;
 }
+
+pie_status apply_one(Problem& pr, const void* x, void* y, cudaStream_t st) { return apply_batch(pr, x, y, 1, st); }
 
 // ---------------------------------------------------------------- right-hand side
 

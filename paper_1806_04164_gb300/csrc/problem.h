@@ -29,8 +29,8 @@ struct LevelDev {
   int32_t* parent = nullptr;   // [nb] parent box number at level l-1
   int8_t* octant = nullptr;    // [nb] octant of the box within its parent
   void* trans = nullptr;       // [316][P] translation operator (far precision)
-  void* S = nullptr;           // [nb][5][P]
-  void* G = nullptr;           // [nb][5][P]
+  void* S = nullptr;           // [max_nrhs][nb][5][P]
+  void* G = nullptr;           // [max_nrhs][nb][5][P]
   void* phase = nullptr;       // [8][P] interpolation phase for children (l < L)
   void* F = nullptr;           // [P][P] filter from level l+1 to l (l < L), F[p][p']
   void* Ft = nullptr;          // [P][P] its transpose
@@ -89,11 +89,11 @@ struct Problem {
   int prof_cap = 0, prof_n = 0;
 
   // work buffers
-  void* coef = nullptr;          // [T][6] complex (io precision)
+  void* coef = nullptr;          // [max_nrhs][T][6] complex (io precision)
   void* coef32 = nullptr;        // [T][6] complex float copy for the MIXED near part
   void* vec = nullptr;           // [N] complex (io precision), adjoint scratch
   void* vec2 = nullptr;          // [N] complex (io precision), single-layer scratch
-  void* pot = nullptr;           // [T][6]
+  void* pot = nullptr;           // [max_nrhs][T][6]
 
   bool near_f32() const { return par.precision != PIE_FP64; }
   bool far_f32() const { return par.precision == PIE_FP32; }
@@ -104,6 +104,7 @@ struct Problem {
 pie_status setup_device(Problem& pr, cudaStream_t st);
 // apply (apply.cu)
 pie_status apply_one(Problem& pr, const void* x, void* y, cudaStream_t st);
+pie_status apply_batch(Problem& pr, const void* x, void* y, int nrhs, cudaStream_t st);
 // records the start (end = false) or end of stage `stage` of the current apply when profiling
 void prof_mark(Problem& pr, int stage, bool end, cudaStream_t st);
 pie_status apply_near_one(Problem& pr, const void* x, void* y, cudaStream_t st);

@@ -729,8 +729,8 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
       lv.il_ptr = upload(pr, ptr, st, s);
       lv.il_idx = upload(pr, idx, st, s);
       lv.il_off = upload(pr, tr.il_off[l], st, s);
-      lv.S = zalloc(pr, sizeof(C2<Rf>) * size_t(lv.nb) * kComp * P, s);
-      lv.G = zalloc(pr, sizeof(C2<Rf>) * size_t(lv.nb) * kComp * P, s);
+      lv.S = zalloc(pr, sizeof(C2<Rf>) * size_t(pr.par.max_nrhs) * size_t(lv.nb) * kComp * P, s);
+      lv.G = zalloc(pr, sizeof(C2<Rf>) * size_t(pr.par.max_nrhs) * size_t(lv.nb) * kComp * P, s);
       lv.trans = zalloc(pr, sizeof(C2<Rf>) * kNoffs * P, s);
       if (s != PIE_OK) return s;
       const double al = tr.box_size(l);
@@ -755,9 +755,10 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
     if (s != PIE_OK) return s;
   }
   const size_t cio = pr.io_f32() ? sizeof(cf) : sizeof(cd);
-  pr.coef = zalloc(pr, cio * 6 * size_t(T), s);
-  pr.pot = zalloc(pr, cio * 6 * size_t(T), s);
-  if (pr.par.precision == PIE_MIXED) pr.coef32 = zalloc(pr, sizeof(cf) * 6 * size_t(T), s);
+  const size_t nr = size_t(pr.par.max_nrhs);
+  pr.coef = zalloc(pr, cio * 6 * size_t(T) * nr, s);
+  pr.pot = zalloc(pr, cio * 6 * size_t(T) * nr, s);
+  if (pr.par.precision == PIE_MIXED) pr.coef32 = zalloc(pr, sizeof(cf) * 6 * size_t(T) * nr, s);
   pr.vec = zalloc(pr, cio * size_t(pr.N), s);
   pr.vec2 = zalloc(pr, cio * size_t(pr.N), s);
   if (s != PIE_OK) return s;

@@ -129,14 +129,18 @@ def test_fp32_near_part_and_far_loss(pg, mesh3, oracle3, dense3):
     print("FP32 full product relative error vs dense:", rel(y, dense3 @ x))
 
 
-def test_batched_columns_and_empty(pg, mesh3):
+@pytest.mark.parametrize("prec", [0, 2])
+def test_batched_columns_and_empty(pg, mesh3, prec):
+    """Batched right-hand sides (max_nrhs = 4, five columns: a batch of four
+    and one of one) equal column-by-column products bit for bit."""
     import torch
-    pr = make(pg, mesh3, 3)
-    X = torch.from_numpy(np.stack([pi.complex_normal(pr.N, s) for s in (1, 2, 3)])).cuda()
-    Y = pr.apply(X)
-    for j in range(3):
-        assert torch.allclose(Y[j], pr.apply(X[j].contiguous()), rtol=0, atol=0)
-    Z = pr.apply(X[:0])
+    pr1 = pg.Problem(pg.Mesh(*mesh3), K, 4, root_side=2.0, precision=prec)
+    pr4 = pg.Problem(pg.Mesh(*mesh3), K, 4, root_side=2.0, precision=prec, max_nrhs=4)
+    X = torch.from_numpy(np.stack([pi.complex_normal(pr1.N, s) for s in (1, 2, 3, 4, 5)])).cuda()
+    Y = pr4.apply(X)
+    for j in range(5):
+        assert torch.equal(Y[j], pr1.apply(X[j].contiguous()))
+    Z = pr4.apply(X[:0])
     assert Z.shape[0] == 0
 
 
