@@ -210,7 +210,9 @@ def run_ours(args):
         gm = None
         if not args.no_gmres:
             gm = gmres_run(pr, args.gmres_tol, k0, barrier, max_over_ranks)
-        launches_per = 1 + 1 + 1 + (pr.L - 3) + (pr.L - 2) + (pr.L - 3) + 1 + 1
+        # coef, near, aggregation, interpolation (L-3), translation (L-2), anterpolation (L-3),
+        # sum/difference patterns, disaggregation, assembly
+        launches_per = 1 + 1 + 1 + (pr.L - 3) + (pr.L - 2) + (pr.L - 3) + 1 + 1 + 1
         results[mode] = dict(pr=pr, ms=ms_max, stage_ms=stage_ms, napplies=napplies, clocks=clk.summary(),
                              e2e_ms=e2e_ms, setup_s=setup_s, launches=launches_per * args.steps,
                              bytes_io=x.numel() * x.element_size(), device_bytes=pr.device_bytes,

@@ -499,35 +499,53 @@ __global__ void k_anterp(int P, const int32_t* __restrict__ parent, const int8_t
   }
 }
 
+// Sum and difference of the incoming leaf patterns over antipodal sample
+// pairs, once per box: GS[b][c][q] = G(q) + G(-q), GD[b][c][q] = G(q) - G(-q)
+// (half grid q), shared by all triangles of the box in the disaggregation.
+template <typename Rf>
+__global__ void k_gsgd(int P, int ntheta, const C2<Rf>* __restrict__ G, C2<Rf>* __restrict__ GS,
+                       C2<Rf>* __restrict__ GD, int64_t sG = 0, int64_t sH = 0) {
+  const int b = blockIdx.x;
+  const int Ph = P / 2;
+  G += blockIdx.y * sG;
+  GS += blockIdx.y * sH;
+  GD += blockIdx.y * sH;
+  for (int i = threadIdx.x; i < kComp * Ph; i += blockDim.x) {
+    const int c = i / Ph, q = i % Ph;
+    const C2<Rf> u = G[((int64_t)b * kComp + c) * P + q];
+    const C2<Rf> v = G[((int64_t)b * kComp + c) * P + antipode(q, ntheta)];
+    GS[((int64_t)b * kComp + c) * Ph + q] = mk<Rf>(u.x + v.x, u.y + v.y);
+    GD[((int64_t)b * kComp + c) * Ph + q] = mk<Rf>(u.x - v.x, u.y - v.y);
+  }
+}
+
 // a6: leaf disaggregation with the receiving (conjugate) patterns.  One
 // thread per triangle; the receiving tables are stored sample-major
 // ([Ph][T], [3][Ph][T]) so that consecutive threads read consecutive
-// triangles, and the incoming pattern of the leaf box is shared through the
+// triangles, and the box's sum / difference patterns are shared through the
 // cache.  Over a sample pair (q, -q):
 // conj(X(q)) G(q) + X(q) G(-q) = Xr (G(q) + G(-q)) - i Xi (G(q) - G(-q)).
 // Adds to pot[t].
 template <typename Rf, typename Rio>
-__global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, int ntheta, const int32_t* __restrict__ leaf_of,
+__global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, const int32_t* __restrict__ leaf_of,
                                                 const C2<Rf>* __restrict__ PiR, const C2<Rf>* __restrict__ MR,
-                                                const C2<Rf>* __restrict__ G, C2<Rio>* __restrict__ pot,
-                                                int64_t sG = 0, int64_t sp = 0) {
+                                                const C2<Rf>* __restrict__ GS, const C2<Rf>* __restrict__ GD,
+                                                C2<Rio>* __restrict__ pot, int64_t sH = 0, int64_t sp = 0) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= T) return;
-  G += blockIdx.y * sG;
-  pot += blockIdx.y * sp;
   const int Ph = P / 2;
-  const C2<Rf>* g = G + (int64_t)leaf_of[t] * kComp * P;
+  GS += blockIdx.y * sH + (int64_t)leaf_of[t] * kComp * Ph;
+  GD += blockIdx.y * sH + (int64_t)leaf_of[t] * kComp * Ph;
+  pot += blockIdx.y * sp;
   C2<Rf> acc[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) acc[i] = mk<Rf>(0, 0);
   for (int q = 0; q < Ph; ++q) {
-    const int qa = antipode(q, ntheta);
     C2<Rf> gs[kComp], gd[kComp];
 #pragma unroll
     for (int c = 0; c < kComp; ++c) {
-      C2<Rf> u = g[c * P + q], v = g[c * P + qa];
-      gs[c] = mk<Rf>(u.x + v.x, u.y + v.y);
-      gd[c] = mk<Rf>(u.x - v.x, u.y - v.y);
+      gs[c] = GS[c * Ph + q];
+      gd[c] = GD[c * Ph + q];
     }
     C2<Rf> pi = PiR[(int64_t)q * T + t];
 #pragma unroll
@@ -710,9 +728,17 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   }
   prof_mark(pr, 5, true, st);
   prof_mark(pr, 6, false, st);
-  k_disagg<Rf, Rio><<<dim3(nblk(pr.T, 256), nr), 256, 0, st>>>(
-      pr.T, P, pr.par.ntheta, pr.leaf_of, static_cast<const C2<Rf>*>(pr.PiR), static_cast<const C2<Rf>*>(pr.MR),
-      static_cast<const C2<Rf>*>(pr.lev[L].G), pot, sl(L), sT);
+  {
+    C2<Rf>* GS = static_cast<C2<Rf>*>(pr.gsgd);
+    C2<Rf>* GD = GS + int64_t(pr.par.max_nrhs) * pr.lev[L].nb * kComp * (P / 2);
+    const int64_t sH = int64_t(pr.lev[L].nb) * kComp * (P / 2);
+    k_gsgd<Rf><<<dim3(unsigned(pr.lev[L].nb), nr), 128, 0, st>>>(P, pr.par.ntheta,
+                                                                 static_cast<const C2<Rf>*>(pr.lev[L].G), GS, GD,
+                                                                 sl(L), sH);
+    k_disagg<Rf, Rio><<<dim3(nblk(pr.T, 256), nr), 256, 0, st>>>(
+        pr.T, P, pr.leaf_of, static_cast<const C2<Rf>*>(pr.PiR), static_cast<const C2<Rf>*>(pr.MR), GS, GD, pot, sH,
+        sT);
+  }
   prof_mark(pr, 6, true, st);
   prof_mark(pr, 7, false, st);
   k_assemble<Rio><<<dim3(nblk(pr.N, 256), nr), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c,

@@ -91,6 +91,7 @@ struct Problem {
   // work buffers
   void* coef = nullptr;          // [max_nrhs][T][6] complex (io precision)
   void* coef32 = nullptr;        // [T][6] complex float copy for the MIXED near part
+  void* gsgd = nullptr;          // 2 x [max_nrhs][nleaf][5][P/2] antipodal sum / difference leaf patterns
   void* vec = nullptr;           // [N] complex (io precision), adjoint scratch
   void* vec2 = nullptr;          // [N] complex (io precision), single-layer scratch
   void* pot = nullptr;           // [max_nrhs][T][6]

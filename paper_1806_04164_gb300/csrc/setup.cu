@@ -756,6 +756,7 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   }
   const size_t cio = pr.io_f32() ? sizeof(cf) : sizeof(cd);
   const size_t nr = size_t(pr.par.max_nrhs);
+  pr.gsgd = zalloc(pr, sizeof(C2<Rf>) * 2 * nr * size_t(pr.lev[L].nb) * kComp * (P / 2), s);
   pr.coef = zalloc(pr, cio * 6 * size_t(T) * nr, s);
   pr.pot = zalloc(pr, cio * 6 * size_t(T) * nr, s);
   if (pr.par.precision == PIE_MIXED) pr.coef32 = zalloc(pr, sizeof(cf) * 6 * size_t(T) * nr, s);
