@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES time-to-tolerance measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 8-right-hand-side batched measurement")
+    ap.add_argument("--no-multimesh", action="store_true",
+                    help="skip the four-mesh, 64-right-hand-side group launch measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
     ap.add_argument("--gmres-tol", type=float, default=1e-6)
     ap.add_argument("--mesh-level", type=int, default=7,
                     help="icosphere subdivision n (L = n levels); 7 is the timed workload, smaller for profiling")
@@ -167,6 +170,7 @@ def run_ours(args):
         t0 = time.time()
         pr = pg.Problem(mesh, k0, nlev, root_side=2.0, precision=prec)
         setup_s = time.time() - t0
+        tuning, tune_ms = (pr.tuning, None) if args.no_autotune else pr.autotune(nrhs=1, reps=5)
         x = torch.from_numpy(x_host).to(pr.torch_dtype).cuda()
         y = torch.empty_like(x)
         for _ in range(args.warmup):
@@ -174,7 +178,6 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        pr.profile_begin(args.steps)
         with ClockSampler(local) as clk:
             torch.cuda.synchronize()
             ev0.record(stream)
@@ -184,8 +187,12 @@ def run_ours(args):
             torch.cuda.synchronize()
         barrier()
         ms = ev0.elapsed_time(ev1)
-        stage_ms, napplies = pr.profile_end()
         ms_max = max_over_ranks(ms)
+        # per-stage CUDA events (stages in order, near part not overlapped)
+        pr.profile_begin(args.steps)
+        for _ in range(args.steps):
+            pr.apply(x, y)
+        stage_ms, napplies = pr.profile_end()
         # end to end through the public API with host buffers
         xh = torch.from_numpy(x_host).to(pr.torch_dtype).pin_memory()
         yh = torch.empty_like(xh).pin_memory()
@@ -214,6 +221,7 @@ def run_ours(args):
         # sum/difference patterns, disaggregation, assembly
         launches_per = 1 + 1 + 1 + (pr.L - 3) + (pr.L - 2) + (pr.L - 3) + 1 + 1 + 1
         results[mode] = dict(pr=pr, ms=ms_max, stage_ms=stage_ms, napplies=napplies, clocks=clk.summary(),
+                             tuning=tuning,
                              e2e_ms=e2e_ms, setup_s=setup_s, launches=launches_per * args.steps,
                              bytes_io=x.numel() * x.element_size(), device_bytes=pr.device_bytes,
                              near_pairs=pr.near_pairs, gmres=gm)
@@ -222,6 +230,8 @@ def run_ours(args):
     if not args.no_batched:
         nb = 8
         prb = pg.Problem(mesh, k0, nlev, root_side=2.0, precision=pg.PIE_MIXED, max_nrhs=nb)
+        if not args.no_autotune:
+            prb.autotune(nrhs=nb, reps=3)
         X = torch.from_numpy(np.stack([pi.complex_normal(mesh.nt + mesh.ne, 1234 + j) for j in range(nb)])).cuda()
         Y = torch.empty_like(X)
         for _ in range(args.warmup):
@@ -235,8 +245,10 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        results["batched"] = dict(nrhs=nb, ms=max_over_ranks(e0.elapsed_time(e1)))
+        results["batched"] = dict(nrhs=nb, ms=max_over_ranks(e0.elapsed_time(e1)), tuning=prb.tuning)
         del prb, X, Y
+    if not args.no_multimesh:
+        results["multimesh"] = multimesh_run(args, stream, barrier, max_over_ranks)
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -275,6 +287,7 @@ def run_ours(args):
         "config": dict(WORKLOAD if nlev == 7 else dict(workload=f"pec_sphere_icosphere{nlev}", N=pr.N, levels=pr.L),
                        precision="mixed", parallelism=f"replicas{world}",
                        l2="working set > L2 (near moments %.1f GB), no flush" % (main["near_pairs"] * 64 / 1e9)),
+        "tuning": main["tuning"],
         "e2e": {"value": world * K / (main["e2e_ms"] * 1e-3), "unit": "matvecs/s",
                 "h2d_bytes_per_step": main["bytes_io"], "d2h_bytes_per_step": main["bytes_io"]},
         "gpu_launches": main["launches"],
@@ -283,12 +296,14 @@ def run_ours(args):
         "stage_share": stage_share,
         "fp64": {"value": world * K / (fp["ms"] * 1e-3), "ms_per_step": fp["ms"] / K,
                  "stage_ms_per_step": {k: v / K for k, v in fp["stage_ms"].items()},
-                 "e2e_value": world * K / (fp["e2e_ms"] * 1e-3), "setup_s": fp["setup_s"],
+                 "e2e_value": world * K / (fp["e2e_ms"] * 1e-3), "setup_s": fp["setup_s"], "tuning": fp["tuning"],
                  "gmres": fp["gmres"]},
         "gmres": main["gmres"],
         "batched8": ({"value": world * K * results["batched"]["nrhs"] / (results["batched"]["ms"] * 1e-3),
                       "unit": "matvecs/s", "nrhs": results["batched"]["nrhs"], "precision": "mixed",
-                      "ms_per_batch": results["batched"]["ms"] / K} if "batched" in results else None),
+                      "ms_per_batch": results["batched"]["ms"] / K, "tuning": results["batched"]["tuning"]}
+                     if "batched" in results else None),
+        "multimesh": results.get("multimesh"),
         "setup_s": main["setup_s"],
         "device_bytes": main["device_bytes"],
         "clocks": main["clocks"],
@@ -296,6 +311,89 @@ def run_ours(args):
     if not args.no_cpu_baseline and nlev == 7:
         line["cpu_baseline"] = cpu_baseline(args.cpu_rows)
     print(json.dumps(line))
+
+
+MULTIMESH = [  # name, mesh generator, root side (0 = bounding box), level range searched
+    ("sphere", lambda pi: pi.icosphere(5), 2.0, (4, 6)),
+    ("cube", lambda pi: pi.cube(32), 1.0, (4, 6)),
+    ("ellipsoid_2_1_1", lambda pi: pi.octasphere(6, (1.0, 0.5, 0.5)), 0.0, (5, 7)),
+    ("cylinder_capped", lambda pi: pi.cylinder(), 0.0, (5, 7)),
+]
+
+
+def multimesh_run(args, stream, barrier, max_over_ranks):
+    """Four meshes of uneven size (20,480 to 40,960 triangles), kR = 1e-2,
+    64 plane-wave right-hand sides each (32 directions on a uniform
+    (theta, phi) grid x 2 polarisations), MIXED, in one group launch (one
+    CUDA graph holding every member's product).  Level count and launch
+    settings per mesh are chosen by the autotuner (set-up, untimed).  One
+    step = one group launch = 4 x 64 products."""
+    import numpy as np
+    import torch
+
+    import paper_1806_04164_gb300 as pg
+    import pie_inputs as pi
+    k0, nrhs = 1e-2, 64
+    th = (np.arange(4) + 0.5) * np.pi / 4
+    ph = np.arange(8) * 2 * np.pi / 8
+    waves = []
+    for t in th:
+        for p in ph:
+            kh = -np.array([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)])
+            e_th = np.array([np.cos(t) * np.cos(p), np.cos(t) * np.sin(p), -np.sin(t)])
+            e_ph = np.array([-np.sin(p), np.cos(p), 0.0])
+            waves += [(kh, e_th), (kh, e_ph)]
+    members, info = [], []
+    t0 = time.time()
+    for name, gen, side, (lmin, lmax) in MULTIMESH:
+        xyz, tri = gen(pi)
+        mesh = pg.Mesh(xyz, tri)
+        if args.no_autotune:
+            L, lms = lmin + 1, {}
+        else:
+            # level search on 8-column products (per-column cost, smaller set-up)
+            L, lms = pg.tune_levels(mesh, k0, lmin, lmax, nrhs=8, root_side=side, precision=pg.PIE_MIXED,
+                                    max_nrhs=8)
+        pr = pg.Problem(mesh, k0, L, root_side=side, precision=pg.PIE_MIXED, max_nrhs=nrhs)
+        tuning = pr.tuning if args.no_autotune else pr.autotune(nrhs=nrhs, reps=3)[0]
+        members.append(pr)
+        info.append(dict(name=name, triangles=pr.T, N=pr.N, levels=L, ms_per_rhs_by_levels=lms, tuning=tuning))
+    setup_s = time.time() - t0
+    xs = [torch.stack([pr.rhs_planewave(kh, pol) for kh, pol in waves]) for pr in members]
+    ys = [torch.empty_like(x) for x in xs]
+    grp = pg.Group(members)
+    for _ in range(args.warmup):
+        grp.apply(xs, ys)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        grp.apply(xs, ys)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    # the same products issued member after member on one stream, for contrast
+    for pr, x, y in zip(members, xs, ys):
+        pr.apply(x, y)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for pr, x, y in zip(members, xs, ys):
+            pr.apply(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / args.steps
+    g = grp.info()
+    out = {"value": len(members) * nrhs / (ms * 1e-3), "unit": "matvecs/s (one mesh, one right-hand side each)",
+           "unknown_matvecs_per_s": sum(m.N for m in members) * nrhs / (ms * 1e-3),
+           "ms_per_launch": ms, "ms_member_by_member": seq_ms, "nrhs": nrhs, "kR": k0, "precision": "mixed",
+           "graphs_captured": g["graphs"], "group_launches": g["launches"], "setup_and_tuning_s": setup_s,
+           "meshes": info}
+    del grp, xs, ys, members
+    torch.cuda.empty_cache()
+    return out
 
 
 def rayleigh_eplane(k0, R, cosg):

@@ -284,6 +284,76 @@ pie_status pie_rhs_potential(pie_problem* pr, const double khat[3], const double
 pie_status pie_nearfield(pie_problem* pr, const void* x, const void* rho, const double* pts, int64_t npts, void* E,
                          void* stream);
 
+/* Launch choices of the product (the paper, one MATLAB process, has none;
+ * they change where and how the stages run, never the arithmetic, so the
+ * product is the same to the last bit under every setting).
+ *  overlap: 1 = the near part (HBM-bound in PIE_MIXED) runs on a second
+ *    stream of the problem, concurrently with the far part (FP64-ALU-bound);
+ *    the two meet before the assembly.  0 = one stream, stages in order.
+ *  near_ctas_per_sm: grid of the near kernel when overlapped, in CTAs of 256
+ *    threads per SM (each warp walks test triangles with a grid stride), so
+ *    that it takes a bounded share of every SM beside the far kernels;
+ *    0 = one warp per test triangle.  0..32.
+ *  rhs_chunk: right-hand sides per pass over the operator, 1..max_nrhs.
+ * Defaults at pie_problem_create: overlap 1, near_ctas_per_sm 2, rhs_chunk
+ * max_nrhs.  Per-stage profiling (pie_profile_begin) runs the stages in
+ * order whatever overlap says. */
+typedef struct pie_tuning {
+  int32_t overlap;
+  int32_t near_ctas_per_sm;
+  int32_t rhs_chunk;
+} pie_tuning;
+
+pie_status pie_problem_get_tuning(const pie_problem* pr, pie_tuning* t);
+/* Errors: PIE_ERR_PARAM (a field out of range). */
+pie_status pie_problem_set_tuning(pie_problem* pr, const pie_tuning* t);
+
+/* Autotuner: times products of nrhs right-hand sides (1..1024; library
+ * scratch, contents irrelevant to the timing) under each candidate setting
+ * -- overlap off, overlap with near_ctas_per_sm in {1, 2, 3, 4, 6, 8, 0},
+ * rhs_chunk in the powers of two up to min(nrhs, max_nrhs) -- by CUDA events
+ * on the stream, median of reps (1..100) after one warm-up each, keeps the
+ * fastest, and returns it (best, host) with its milliseconds per
+ * right-hand side (best_ms, host, may be NULL).  The search is greedy: the
+ * overlap grid at the largest rhs_chunk first, then rhs_chunk.  Allocates
+ * 2 x nrhs x N complex of scratch for its duration; synchronises the stream.
+ * Errors: PIE_ERR_PARAM, PIE_ERR_OOM, PIE_ERR_CUDA. */
+pie_status pie_problem_autotune(pie_problem* pr, int nrhs, int reps, pie_tuning* best, double* best_ms,
+                                void* stream);
+
+/* Level count per mesh: builds the problem of mesh m at k0 with base's other
+ * parameters for every L in [lmin, lmax] whose leaf box admits the mesh
+ * (leaf side >= 1.5 x the longest edge; others are skipped), autotunes each
+ * for nrhs right-hand sides, and returns the L with the fewest milliseconds
+ * per right-hand side (best_levels, host).  ms_per_level (host, may be NULL)
+ * receives lmax - lmin + 1 entries, 0 where L was skipped.  The product's
+ * accuracy does not depend on L at fixed (tau, kappa_a, ntheta).  Each
+ * candidate is set up and destroyed in turn (peak memory: one problem).
+ * Errors: PIE_ERR_PARAM, PIE_ERR_LEAF (no admissible L), the set-up errors. */
+pie_status pie_tune_levels(const pie_mesh* m, double k0, const pie_params* base, int lmin, int lmax, int nrhs,
+                           void* stream, int* best_levels, double* ms_per_level);
+
+/* Multi-mesh batch: several problems (meshes of uneven size, any
+ * wavenumbers and precisions) applied to nrhs right-hand sides each in ONE
+ * launch.  pie_group_apply captures, on first use of a given set of
+ * buffers, the products of all members into one CUDA graph -- each member on
+ * its own branch, so that the small stages of one mesh fill the SMs left
+ * idle by another -- and launches that graph on the stream; later calls
+ * with the same (x, y, nrhs) relaunch it (the graphs of the four most recent
+ * buffer sets are kept).  x[i], y[i]: device buffers of member i, N_i x nrhs
+ * complex in that member's dtype (PIE_C64 for PIE_FP32 problems, PIE_C128
+ * otherwise), column-major as in pie_apply.  Members keep their own state:
+ * a member must not be applied by other calls while a group launch that
+ * holds it may run, nor destroyed before the group; profiling must be off.
+ * pie_group_info: graphs captured so far and group launches (host, may be
+ * NULL).  Errors: PIE_ERR_PARAM (n < 1, NULL member or buffer, nrhs out of
+ * range, a member profiling), PIE_ERR_CUDA. */
+typedef struct pie_group pie_group;
+pie_status pie_group_create(pie_problem* const* members, int n, pie_group** out);
+pie_status pie_group_apply(pie_group* g, const void* const* x, void* const* y, int nrhs, void* stream);
+pie_status pie_group_info(const pie_group* g, int64_t* graphs, int64_t* launches);
+void pie_group_destroy(pie_group* g);
+
 #ifdef __cplusplus
 }
 #endif

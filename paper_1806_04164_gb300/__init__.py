@@ -43,6 +43,13 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("leaf_size", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("overlap", ctypes.c_int32), ("near_ctas_per_sm", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32)]
+
+    def as_dict(self):
+        return dict(overlap=self.overlap, near_ctas_per_sm=self.near_ctas_per_sm, rhs_chunk=self.rhs_chunk)
+
+
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
 
@@ -53,7 +60,8 @@ EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_
            "pie_problem_level", "pie_problem_near", "pie_apply", "pie_apply_near", "pie_problem_stage", "pie_rhs_planewave",
            "pie_farfield", "pie_solve", "pie_profile_begin", "pie_profile_end", "pie_apply_near_noalloc", "pie_apply_t",
            "pie_farfield_adjoint", "pie_apply_single_layer", "pie_solve_single_layer", "pie_rhs_potential",
-           "pie_nearfield"]
+           "pie_nearfield", "pie_problem_get_tuning", "pie_problem_set_tuning", "pie_problem_autotune",
+           "pie_tune_levels", "pie_group_create", "pie_group_apply", "pie_group_info", "pie_group_destroy"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -96,6 +104,15 @@ def lib():
         L.pie_profile_begin.argtypes = [vp, i32]
         L.pie_profile_end.argtypes = [vp, PD, P32]
         L.pie_solve.argtypes = [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
+        PT = ctypes.POINTER(Tuning)
+        L.pie_problem_get_tuning.argtypes = [vp, PT]
+        L.pie_problem_set_tuning.argtypes = [vp, PT]
+        L.pie_problem_autotune.argtypes = [vp, i32, i32, PT, PD, vp]
+        L.pie_tune_levels.argtypes = [vp, dbl, ctypes.POINTER(Params), i32, i32, i32, vp, P32, PD]
+        L.pie_group_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+        L.pie_group_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, vp]
+        L.pie_group_info.argtypes = [vp, P64, P64]
+        L.pie_group_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -350,7 +367,75 @@ class Problem:
         return x, dict(iterations=st.iterations, rel_residual=st.rel_residual, seconds=st.seconds,
                        converged=code == 0)
 
+    @property
+    def tuning(self):
+        """Launch settings of the product (pie_problem_get_tuning), as a dict."""
+        t = Tuning()
+        _check(lib().pie_problem_get_tuning(self.handle, ctypes.byref(t)))
+        return t.as_dict()
+
+    @tuning.setter
+    def tuning(self, d):
+        t = Tuning(**{**self.tuning, **d})
+        _check(lib().pie_problem_set_tuning(self.handle, ctypes.byref(t)))
+
+    def autotune(self, nrhs=1, reps=5, stream=None):
+        """Time the launch settings and keep the fastest (pie_problem_autotune);
+        returns (settings dict, milliseconds per right-hand side)."""
+        t = Tuning()
+        ms = ctypes.c_double()
+        _check(lib().pie_problem_autotune(self.handle, nrhs, reps, ctypes.byref(t), ctypes.byref(ms),
+                                          _stream(stream)))
+        return t.as_dict(), ms.value
+
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
             _lib.pie_problem_destroy(self.handle)
+            self.handle = None
+
+
+def tune_levels(mesh, k0, lmin, lmax, nrhs=1, root_side=0.0, tau=DEFAULT_TAU, kappa_a=DEFAULT_KAPPA_A,
+                ntheta=DEFAULT_NTHETA, precision=PIE_FP64, max_nrhs=1, stream=None):
+    """Level count with the fastest autotuned product for this mesh
+    (pie_tune_levels); returns (L, {L: ms per right-hand side})."""
+    p = Params(lmin, root_side, tau, kappa_a, ntheta, precision, max_nrhs)
+    best = ctypes.c_int32()
+    ms = np.zeros(lmax - lmin + 1, np.float64)
+    _check(lib().pie_tune_levels(mesh.handle, float(k0), ctypes.byref(p), lmin, lmax, nrhs, _stream(stream),
+                                 ctypes.byref(best), _ptr(ms, ctypes.c_double)))
+    return best.value, {lmin + i: float(v) for i, v in enumerate(ms) if v > 0}
+
+
+class Group:
+    """Several problems applied in one CUDA-graph launch (pie_group_*)."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        arr = (ctypes.c_void_p * len(self.problems))(*[p.handle for p in self.problems])
+        h = ctypes.c_void_p()
+        _check(lib().pie_group_create(arr, len(self.problems), ctypes.byref(h)))
+        self.handle = h
+
+    def apply(self, xs, ys, stream=None):
+        """ys[i] = Z_i xs[i] for all members at once; xs[i], ys[i]: device
+        tensors [nrhs, N_i] (the same nrhs for all).  Keep ys (and xs) alive
+        and reuse them: the captured graph is tied to their addresses."""
+        xs = [_dense(x) for x in xs]
+        nrhs = xs[0].shape[0] if xs[0].dim() == 2 else 1
+        for p, x, y in zip(self.problems, xs, ys):
+            assert x.is_cuda and y.is_cuda and x.dtype == p.torch_dtype and y.dtype == p.torch_dtype
+            assert x.numel() == nrhs * p.N and y.numel() == nrhs * p.N and y.is_contiguous()
+        xa = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        ya = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+        _check(lib().pie_group_apply(self.handle, xa, ya, nrhs, _stream(stream)))
+        return ys
+
+    def info(self):
+        g, n = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pie_group_info(self.handle, ctypes.byref(g), ctypes.byref(n)))
+        return dict(graphs=g.value, launches=n.value)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.pie_group_destroy(self.handle)
             self.handle = None

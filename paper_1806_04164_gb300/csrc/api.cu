@@ -5,14 +5,7 @@
 #include <new>
 #include <string>
 
-#include "problem.h"
-
-struct pie_mesh {
-  pie::Mesh m;
-};
-struct pie_problem {
-  pie::Problem p;
-};
+#include "handles.h"
 
 namespace pie {
 static thread_local std::string g_err;
@@ -86,6 +79,11 @@ static void free_profile(Problem& pr) {
 
 static void free_problem(Problem& pr) {
   free_profile(pr);
+  if (pr.side) cudaStreamSynchronize(pr.side), cudaStreamDestroy(pr.side);
+  if (pr.ev_fork) cudaEventDestroy(pr.ev_fork);
+  if (pr.ev_join) cudaEventDestroy(pr.ev_join);
+  pr.side = nullptr;
+  pr.ev_fork = pr.ev_join = nullptr;
   for (void* p : pr.allocs) cudaFree(p);
   pr.allocs.clear();
 }
@@ -212,7 +210,7 @@ pie_status pie_problem_near(const pie_problem* h, int64_t* nlist, int64_t* ptr, 
   return PIE_OK;
 }
 
-static pie_status apply_cols(pie_problem* h, const void* x, void* y, int nrhs, int dtype, void* stream, bool near) {
+static pie_status apply_api(pie_problem* h, const void* x, void* y, int nrhs, int dtype, void* stream, bool near) {
   if (!h || (!x && nrhs > 0) || (!y && nrhs > 0) || nrhs < 0) {
     set_error("pie_apply: invalid argument");
     return PIE_ERR_PARAM;
@@ -233,22 +231,17 @@ static pie_status apply_cols(pie_problem* h, const void* x, void* y, int nrhs, i
     }
     return PIE_OK;
   }
-  // batches of up to max_nrhs right-hand sides share each pass over the operator
-  for (int j = 0; j < nrhs; j += pr.par.max_nrhs) {
-    const int nb = std::min(pr.par.max_nrhs, nrhs - j);
-    pie_status s = apply_batch(pr, static_cast<const char*>(x) + es * size_t(pr.N) * j,
-                               static_cast<char*>(y) + es * size_t(pr.N) * j, nb, st);
-    if (s != PIE_OK) return s;
-  }
-  return PIE_OK;
+  // batches of up to tune.rhs_chunk (<= max_nrhs) right-hand sides share
+  // each pass over the operator
+  return pie::apply_cols(pr, x, y, nrhs, st);
 }
 
 pie_status pie_apply(pie_problem* h, const void* x, void* y, int nrhs, int dtype, void* stream) {
-  return apply_cols(h, x, y, nrhs, dtype, stream, false);
+  return apply_api(h, x, y, nrhs, dtype, stream, false);
 }
 
 pie_status pie_apply_near(pie_problem* h, const void* x, void* y, int nrhs, int dtype, void* stream) {
-  return apply_cols(h, x, y, nrhs, dtype, stream, true);
+  return apply_api(h, x, y, nrhs, dtype, stream, true);
 }
 
 pie_status pie_apply_t(pie_problem* h, const void* x, void* y, int nrhs, int dtype, int conj, void* stream) {

@@ -2,6 +2,7 @@
 // local coefficients, near pair products, leaf aggregation, interpolation,
 // translation (Eq. (5) operators), anterpolation, leaf disaggregation and
 // Galerkin assembly (Section 2).
+#include <algorithm>
 #include <cstdio>
 #include <type_traits>
 
@@ -65,65 +66,68 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
                                               const int64_t* __restrict__ row_ptr, const C2<Rm>* __restrict__ mom,
                                               const C2<Rm>* __restrict__ coef, Rm mu0, C2<Rio>* __restrict__ pot,
                                               int nrhs = 1, int64_t sc = 0, int64_t sp = 0) {
-  int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (t >= T) return;
+  const int lane = threadIdx.x & 31;
   // right-hand sides r0 .. r0 + RB - 1 share every moment load
   const int r0 = blockIdx.y * RB;
-  const int b = leaf_of[t];
-  const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
-  const int64_t e0 = row_ptr[t];
-  const int len = int(row_ptr[t + 1] - e0);
-  C2<Rm> acc[RB][6];
+  // one warp per test triangle, with a grid stride when the grid is smaller
+  // than T warps (a bounded share of the SMs beside the far part)
+  const int64_t wstride = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < T; t += wstride) {
+    const int b = leaf_of[t];
+    const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
+    const int64_t e0 = row_ptr[t];
+    const int len = int(row_ptr[t + 1] - e0);
+    C2<Rm> acc[RB][6];
 #pragma unroll
-  for (int r = 0; r < RB; ++r)
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) acc[r][i] = mk<Rm>(0, 0);
-  // the row is the concatenation of the near boxes' source ranges; lanes walk
-  // it flat (32 consecutive entries per step), each lane keeping a cursor on
-  // the near box that holds its position
-  int qi = q0;
-  for (int j = lane; j < len; j += 32) {
-    while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
-    const int64_t s = leaf_start[near_idx[qi]] + (j - near_off[qi]);
-    const int64_t ee = e0 + j;
-    C2<Rm> m0 = mom[ee];
-    C2<Rm> mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
-    C2<Rm> ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
-    C2<Rm> mts = mom[7 * nnz + ee];
+      for (int i = 0; i < 6; ++i) acc[r][i] = mk<Rm>(0, 0);
+    // the row is the concatenation of the near boxes' source ranges; lanes walk
+    // it flat (32 consecutive entries per step), each lane keeping a cursor on
+    // the near box that holds its position
+    int qi = q0;
+    for (int j = lane; j < len; j += 32) {
+      while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
+      const int64_t s = leaf_start[near_idx[qi]] + (j - near_off[qi]);
+      const int64_t ee = e0 + j;
+      C2<Rm> m0 = mom[ee];
+      C2<Rm> mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
+      C2<Rm> ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
+      C2<Rm> mts = mom[7 * nnz + ee];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        if (r0 + r >= nrhs) break;
+        const C2<Rm>* c = coef + (r0 + r) * sc + 6 * s;
+        C2<Rm> a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
+        cfma(acc[r][0], a, mts);
+        cfma(acc[r][0], b0, mt0);
+        cfma(acc[r][0], b1, mt1);
+        cfma(acc[r][0], b2, mt2);
+        cfma(acc[r][1], a, ms0);
+        cfma(acc[r][1], b0, m0);
+        cfma(acc[r][2], a, ms1);
+        cfma(acc[r][2], b1, m0);
+        cfma(acc[r][3], a, ms2);
+        cfma(acc[r][3], b2, m0);
+        cfma(acc[r][4], sg, m0);
+        cfma(acc[r][5], dd, m0);
+      }
+    }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       if (r0 + r >= nrhs) break;
-      const C2<Rm>* c = coef + (r0 + r) * sc + 6 * s;
-      C2<Rm> a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
-      cfma(acc[r][0], a, mts);
-      cfma(acc[r][0], b0, mt0);
-      cfma(acc[r][0], b1, mt1);
-      cfma(acc[r][0], b2, mt2);
-      cfma(acc[r][1], a, ms0);
-      cfma(acc[r][1], b0, m0);
-      cfma(acc[r][2], a, ms1);
-      cfma(acc[r][2], b1, m0);
-      cfma(acc[r][3], a, ms2);
-      cfma(acc[r][3], b2, m0);
-      cfma(acc[r][4], sg, m0);
-      cfma(acc[r][5], dd, m0);
-    }
-  }
 #pragma unroll
-  for (int r = 0; r < RB; ++r) {
-    if (r0 + r >= nrhs) break;
+      for (int i = 0; i < 6; ++i) {
+        acc[r][i].x = warp_sum(acc[r][i].x);
+        acc[r][i].y = warp_sum(acc[r][i].y);
+      }
+      if (lane == 0) {
+        C2<Rio>* o = pot + (r0 + r) * sp + 6 * t;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      acc[r][i].x = warp_sum(acc[r][i].x);
-      acc[r][i].y = warp_sum(acc[r][i].y);
-    }
-    if (lane == 0) {
-      C2<Rio>* o = pot + (r0 + r) * sp + 6 * t;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) o[i] = mk<Rio>(Rio(mu0 * acc[r][i].x), Rio(mu0 * acc[r][i].y));
-      o[4] = cvt<Rio>(acc[r][4]);
-      o[5] = cvt<Rio>(acc[r][5]);
+        for (int i = 0; i < 4; ++i) o[i] = mk<Rio>(Rio(mu0 * acc[r][i].x), Rio(mu0 * acc[r][i].y));
+        o[4] = cvt<Rio>(acc[r][4]);
+        o[5] = cvt<Rio>(acc[r][5]);
+      }
     }
   }
 }
@@ -569,22 +573,31 @@ __global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, const int32_t*
   }
   C2<Rio>* o = pot + 6 * t;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    o[i].x = Rio(double(o[i].x) + double(acc[i].x));
-    o[i].y = Rio(double(o[i].y) + double(acc[i].y));
-  }
+  for (int i = 0; i < 6; ++i) o[i] = mk<Rio>(Rio(acc[i].x), Rio(acc[i].y));
+}
+
+// Per-triangle potential j of the product: near + far (each rounded to the
+// io precision, summed in double, rounded again), or pot alone.
+template <typename Rio>
+__device__ __forceinline__ C2<Rio> pot_sum(const C2<Rio>* pot, const C2<Rio>* pot2, int64_t j) {
+  if (!pot2) return pot[j];
+  const C2<Rio> a = pot2[j], b = pot[j];
+  return mk<Rio>(Rio(double(a.x) + double(b.x)), Rio(double(a.y) + double(b.y)));
 }
 
 // a7: Galerkin testing of the per-triangle potentials (Section 2):
 // RWG m: sum over its two triangles of c [U + (c_t - p).V] + 2c T1; pulse t: T2.
+// pot2 (may be null): near-part potentials, added to pot first.
 template <typename Rio>
 __global__ void k_assemble(int64_t N, int64_t E, const int32_t* __restrict__ edge_tt,
                            const int8_t* __restrict__ edge_k, const double* __restrict__ tri_c,
                            const double* __restrict__ tri_dcp, const int64_t* __restrict__ inv_perm,
-                           const C2<Rio>* __restrict__ pot, C2<Rio>* __restrict__ y, int64_t sp = 0, int64_t sy = 0) {
+                           const C2<Rio>* __restrict__ pot, C2<Rio>* __restrict__ y, int64_t sp = 0, int64_t sy = 0,
+                           const C2<Rio>* __restrict__ pot2 = nullptr) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   pot += blockIdx.y * sp;
+  if (pot2) pot2 += blockIdx.y * sp;
   y += blockIdx.y * sy;
   if (i < E) {
     double yr = 0, yi = 0;
@@ -594,7 +607,9 @@ __global__ void k_assemble(int64_t N, int64_t E, const int32_t* __restrict__ edg
       int k = edge_k[2 * i + side];
       double c = tri_c[3 * t + k];
       const double* dcp = tri_dcp + 9 * t + 3 * k;
-      const C2<Rio>* p = pot + 6 * t;
+      C2<Rio> p[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) p[j] = pot_sum(pot, pot2, 6 * t + j);
       double ur = double(p[0].x) + dcp[0] * double(p[1].x) + dcp[1] * double(p[2].x) + dcp[2] * double(p[3].x);
       double ui = double(p[0].y) + dcp[0] * double(p[1].y) + dcp[1] * double(p[2].y) + dcp[2] * double(p[3].y);
       yr += c * (ur + 2.0 * double(p[4].x));
@@ -603,7 +618,7 @@ __global__ void k_assemble(int64_t N, int64_t E, const int32_t* __restrict__ edg
     y[i] = mk<Rio>(Rio(yr), Rio(yi));
   } else {
     int64_t t = inv_perm[i - E];
-    y[i] = pot[6 * t + 5];
+    y[i] = pot_sum(pot, pot2, 6 * t + 5);
   }
 }
 
@@ -658,14 +673,30 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   k_coef<Rio><<<dim3(nblk(pr.T, 256), nr), 256, 0, st>>>(pr.T, pr.E, x, pr.perm, pr.tri_edge, pr.tri_c, pr.tri_dcp,
                                                          w2e, coef, coef32, sN, sT);
   prof_mark(pr, 0, true, st);
+  // near part into pot2, far part into pot.  With tune.overlap the near part
+  // runs on the side stream (HBM-bound, a bounded grid) while the far part
+  // (FP64-ALU-bound) runs here; per-stage profiling keeps them in order.
+  const bool profiling = pr.prof_n < pr.prof_cap;
+  const bool overlap = pr.tune.overlap && !profiling;
+  C2<Rio>* pot2 = static_cast<C2<Rio>*>(pr.pot2);
+  cudaStream_t sn = st;
+  unsigned near_grid = nblk(pr.T * 32, 256);
+  if (overlap) {
+    pie_status s = cuda_check(cudaEventRecord(pr.ev_fork, st), "fork");
+    if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(pr.side, pr.ev_fork, 0), "fork");
+    if (s != PIE_OK) return s;
+    sn = pr.side;
+    if (pr.tune.near_ctas_per_sm > 0)
+      near_grid = std::min<unsigned>(near_grid, unsigned(pr.nsm * pr.tune.near_ctas_per_sm));
+  }
   prof_mark(pr, 1, false, st);
   // the near part reads each pair's moments once for RB right-hand sides
   // (RB chosen per call: a wide accumulator set costs occupancy when unused)
   auto near_launch = [&](auto rb) {
     constexpr int RB = decltype(rb)::value;
-    k_near<Rm, Rio, RB><<<dim3(nblk(pr.T * 32, 256), unsigned((nrhs + RB - 1) / RB)), 256, 0, st>>>(
+    k_near<Rm, Rio, RB><<<dim3(near_grid, unsigned((nrhs + RB - 1) / RB)), 256, 0, sn>>>(
         pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
-        static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot, nrhs, sT, sT);
+        static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot2, nrhs, sT, sT);
   };
   if (nrhs == 1)
     near_launch(std::integral_constant<int, 1>());
@@ -675,6 +706,10 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
     near_launch(std::integral_constant<int, 4>());
   else
     near_launch(std::integral_constant<int, 8>());
+  if (overlap) {
+    pie_status s = cuda_check(cudaEventRecord(pr.ev_join, sn), "join");
+    if (s != PIE_OK) return s;
+  }
   prof_mark(pr, 1, true, st);
   const int tpb = P < 1024 ? ((P + 31) / 32) * 32 : 1024;
   const C2<Rf>* Pi = static_cast<const C2<Rf>*>(pr.Pi);
@@ -740,9 +775,13 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
         sT);
   }
   prof_mark(pr, 6, true, st);
+  if (overlap) {
+    pie_status s = cuda_check(cudaStreamWaitEvent(st, pr.ev_join, 0), "join");
+    if (s != PIE_OK) return s;
+  }
   prof_mark(pr, 7, false, st);
   k_assemble<Rio><<<dim3(nblk(pr.N, 256), nr), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c,
-                                                             pr.tri_dcp, pr.inv_perm, pot, y, sT, sN);
+                                                             pr.tri_dcp, pr.inv_perm, pot, y, sT, sN, pot2);
   prof_mark(pr, 7, true, st);
   if (pr.prof_n < pr.prof_cap) ++pr.prof_n;
   return cuda_check(cudaGetLastError(), "apply launch");
@@ -795,6 +834,22 @@ pie_status apply_batch(Problem& pr, const void* x, void* y, int nrhs, cudaStream
 }
 
 pie_status apply_one(Problem& pr, const void* x, void* y, cudaStream_t st) { return apply_batch(pr, x, y, 1, st); }
+
+pie_status prepare_apply(Problem& pr) {
+  if (pr.par.ntheta != 8) return PIE_OK;
+  return pr.far_f32() ? fft_prepare<8, float>() : fft_prepare<8, double>();
+}
+
+pie_status apply_cols(Problem& pr, const void* x, void* y, int nrhs, cudaStream_t st) {
+  const size_t col = (pr.io_f32() ? sizeof(cf) : sizeof(cd)) * size_t(pr.N);
+  const int chunk = std::max(1, std::min(pr.tune.rhs_chunk, pr.par.max_nrhs));
+  for (int j = 0; j < nrhs; j += chunk) {
+    pie_status s = apply_batch(pr, static_cast<const char*>(x) + col * j, static_cast<char*>(y) + col * j,
+                               std::min(chunk, nrhs - j), st);
+    if (s != PIE_OK) return s;
+  }
+  return PIE_OK;
+}
 
 // ---------------------------------------------------------------- right-hand side
 

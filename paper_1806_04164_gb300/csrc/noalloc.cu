@@ -10,7 +10,7 @@
 // calls no allocating routine.
 #include <mutex>
 
-#include "problem.h"
+#include "handles.h"
 
 namespace pie {
 
@@ -47,9 +47,6 @@ static pie_status scratch_address(void** out) {
 
 }  // namespace pie
 
-struct pie_problem {
-  pie::Problem p;
-};
 
 using namespace pie;
 

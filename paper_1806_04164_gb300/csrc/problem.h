@@ -94,7 +94,14 @@ struct Problem {
   void* gsgd = nullptr;          // 2 x [max_nrhs][nleaf][5][P/2] antipodal sum / difference leaf patterns
   void* vec = nullptr;           // [N] complex (io precision), adjoint scratch
   void* vec2 = nullptr;          // [N] complex (io precision), single-layer scratch
-  void* pot = nullptr;           // [max_nrhs][T][6]
+  void* pot = nullptr;           // [max_nrhs][T][6] far-part potentials (near part too when pot2 is unused)
+  void* pot2 = nullptr;          // [max_nrhs][T][6] near-part potentials of the full product
+  // the near part runs on `side`, concurrently with the far part on the
+  // caller's stream, when tune.overlap is set
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int nsm = 0;                   // SMs of the device
+  pie_tuning tune{1, 2, 1};
 
   bool near_f32() const { return par.precision != PIE_FP64; }
   bool far_f32() const { return par.precision == PIE_FP32; }
@@ -106,6 +113,10 @@ pie_status setup_device(Problem& pr, cudaStream_t st);
 // apply (apply.cu)
 pie_status apply_one(Problem& pr, const void* x, void* y, cudaStream_t st);
 pie_status apply_batch(Problem& pr, const void* x, void* y, int nrhs, cudaStream_t st);
+// x, y: N x nrhs columns, passes of tune.rhs_chunk columns
+pie_status apply_cols(Problem& pr, const void* x, void* y, int nrhs, cudaStream_t st);
+// one-time kernel attributes of the product (not allowed inside a stream capture)
+pie_status prepare_apply(Problem& pr);
 // records the start (end = false) or end of stage `stage` of the current apply when profiling
 void prof_mark(Problem& pr, int stage, bool end, cudaStream_t st);
 pie_status apply_near_one(Problem& pr, const void* x, void* y, cudaStream_t st);

@@ -759,11 +759,20 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   pr.gsgd = zalloc(pr, sizeof(C2<Rf>) * 2 * nr * size_t(pr.lev[L].nb) * kComp * (P / 2), s);
   pr.coef = zalloc(pr, cio * 6 * size_t(T) * nr, s);
   pr.pot = zalloc(pr, cio * 6 * size_t(T) * nr, s);
+  pr.pot2 = zalloc(pr, cio * 6 * size_t(T) * nr, s);
   if (pr.par.precision == PIE_MIXED) pr.coef32 = zalloc(pr, sizeof(cf) * 6 * size_t(T) * nr, s);
   pr.vec = zalloc(pr, cio * size_t(pr.N), s);
   pr.vec2 = zalloc(pr, cio * size_t(pr.N), s);
   if (s != PIE_OK) return s;
   if ((s = cuda_check(cudaGetLastError(), "setup launch")) != PIE_OK) return s;
+  int dev = 0;
+  if ((s = cuda_check(cudaGetDevice(&dev), "device")) != PIE_OK) return s;
+  if ((s = cuda_check(cudaDeviceGetAttribute(&pr.nsm, cudaDevAttrMultiProcessorCount, dev), "SM count")) != PIE_OK)
+    return s;
+  if ((s = cuda_check(cudaStreamCreateWithFlags(&pr.side, cudaStreamNonBlocking), "side stream")) != PIE_OK) return s;
+  if ((s = cuda_check(cudaEventCreateWithFlags(&pr.ev_fork, cudaEventDisableTiming), "event")) != PIE_OK) return s;
+  if ((s = cuda_check(cudaEventCreateWithFlags(&pr.ev_join, cudaEventDisableTiming), "event")) != PIE_OK) return s;
+  pr.tune = pie_tuning{1, 2, pr.par.max_nrhs};
   return cuda_check(cudaStreamSynchronize(st), "setup");
 }
 

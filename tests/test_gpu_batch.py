@@ -1,0 +1,138 @@
+"""Launch settings, the autotuner and multi-mesh groups.  None of them may
+change the product: every setting, and a group's single graph launch over
+several meshes of uneven size, must give the members' own products bit for
+bit."""
+import numpy as np
+import pytest
+
+import pie_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+K = 0.01
+
+
+@pytest.fixture(scope="module")
+def pg():
+    from tests._lib import ensure_built
+    ensure_built()
+    import paper_1806_04164_gb300 as pg
+    return pg
+
+
+def columns(n, nrhs, seed):
+    import torch
+    return torch.from_numpy(np.stack([pi.complex_normal(n, seed + j) for j in range(nrhs)])).cuda()
+
+
+SETTINGS = [dict(overlap=0, near_ctas_per_sm=0, rhs_chunk=4), dict(overlap=1, near_ctas_per_sm=1, rhs_chunk=4),
+            dict(overlap=1, near_ctas_per_sm=3, rhs_chunk=2), dict(overlap=1, near_ctas_per_sm=0, rhs_chunk=1),
+            dict(overlap=0, near_ctas_per_sm=5, rhs_chunk=3)]
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_settings_do_not_change_the_product(pg, prec):
+    import torch
+    pr = pg.Problem(pg.Mesh(*pi.icosphere(3)), K, 4, root_side=2.0, precision=prec, max_nrhs=4)
+    assert pr.tuning == dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=4)
+    X = columns(pr.N, 5, 11)
+    ref = pr.apply(X)
+    torch.cuda.synchronize()
+    for s in SETTINGS:
+        pr.tuning = s
+        assert pr.tuning == s
+        assert torch.equal(pr.apply(X), ref), s
+
+
+def test_tuning_rejects_out_of_range(pg):
+    pr = pg.Problem(pg.Mesh(*pi.icosphere(2)), K, 3, root_side=2.0, max_nrhs=2)
+    for bad in (dict(overlap=2), dict(near_ctas_per_sm=-1), dict(near_ctas_per_sm=33), dict(rhs_chunk=0),
+                dict(rhs_chunk=3)):
+        with pytest.raises(pg.PieError) as ei:
+            pr.tuning = bad
+        assert ei.value.code == 1
+    assert pr.tuning == dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=2)
+
+
+def test_autotune_keeps_the_product(pg):
+    import torch
+    pr = pg.Problem(pg.Mesh(*pi.icosphere(3)), K, 4, root_side=2.0, precision=pg.PIE_MIXED, max_nrhs=4)
+    X = columns(pr.N, 4, 21)
+    ref = pr.apply(X)
+    best, ms = pr.autotune(nrhs=4, reps=3)
+    assert ms > 0
+    assert best == pr.tuning
+    assert best["overlap"] in (0, 1) and 0 <= best["near_ctas_per_sm"] <= 32 and 1 <= best["rhs_chunk"] <= 4
+    assert torch.equal(pr.apply(X), ref)
+
+
+def test_tune_levels_picks_an_admissible_level(pg):
+    import torch
+    mesh = pg.Mesh(*pi.icosphere(3))
+    L, ms = pg.tune_levels(mesh, K, 3, 8, nrhs=1, root_side=2.0, precision=pg.PIE_MIXED)
+    # leaf side 2 / 2^(L-1) must stay >= 1.5 x the longest edge (0.165 m here)
+    assert set(ms) == {3, 4} and L in ms and ms[L] == min(ms.values())
+    x = torch.from_numpy(pi.complex_normal(mesh.nt + mesh.ne, 31)).cuda()
+    y3 = pg.Problem(mesh, K, 3, root_side=2.0, precision=pg.PIE_MIXED).apply(x)
+    yL = pg.Problem(mesh, K, L, root_side=2.0, precision=pg.PIE_MIXED).apply(x)
+    assert (torch.linalg.norm(yL - y3) / torch.linalg.norm(y3)).item() < 1e-3
+
+
+def group_members(pg):
+    return [
+        pg.Problem(pg.Mesh(*pi.icosphere(3)), K, 4, root_side=2.0, precision=pg.PIE_FP64, max_nrhs=2),
+        pg.Problem(pg.Mesh(*pi.cube(8)), K, 3, root_side=1.0, precision=pg.PIE_MIXED, max_nrhs=3),
+        pg.Problem(pg.Mesh(*pi.octasphere(3, (1.0, 0.5, 0.5))), K, 3, precision=pg.PIE_MIXED, max_nrhs=1),
+        pg.Problem(pg.Mesh(*pi.cylinder(nseg=16, nrings=2, nrows=8)), K, 3, precision=pg.PIE_FP64, max_nrhs=3),
+    ]
+
+
+def test_group_launch_equals_member_products(pg):
+    import torch
+    mem = group_members(pg)
+    assert len({p.N for p in mem}) == 4
+    grp = pg.Group(mem)
+    nrhs = 3
+    xs = [columns(p.N, nrhs, 40 + 5 * i) for i, p in enumerate(mem)]
+    ys = [torch.empty_like(x) for x in xs]
+    refs = [p.apply(x) for p, x in zip(mem, xs)]
+    grp.apply(xs, ys)
+    torch.cuda.synchronize()
+    for y, r in zip(ys, refs):
+        assert torch.equal(y, r)
+    # the same buffers relaunch the captured graph
+    for y in ys:
+        y.zero_()
+    grp.apply(xs, ys)
+    torch.cuda.synchronize()
+    assert all(torch.equal(y, r) for y, r in zip(ys, refs))
+    assert grp.info() == dict(graphs=1, launches=2)
+    # a changed member setting is captured anew, with the same result
+    mem[0].tuning = dict(overlap=0)
+    grp.apply(xs, ys)
+    torch.cuda.synchronize()
+    assert all(torch.equal(y, r) for y, r in zip(ys, refs))
+    assert grp.info() == dict(graphs=2, launches=3)
+    # new inputs through the same buffers: the graph reads them
+    for x in xs:
+        x.mul_(-1j)
+    grp.apply(xs, ys)
+    torch.cuda.synchronize()
+    for y, r in zip(ys, refs):
+        # the MIXED members round the near part in float: agree to ~1e-7
+        assert (torch.linalg.norm(y + 1j * r) / torch.linalg.norm(r)).item() < 1e-6
+
+
+def test_group_rejects_bad_arguments(pg):
+    mem = group_members(pg)[:2]
+    with pytest.raises(pg.PieError):
+        pg.Group([mem[0], mem[0]])
+    grp = pg.Group(mem)
+    mem[1].profile_begin(1)
+    import torch
+    xs = [columns(p.N, 1, 60 + i) for i, p in enumerate(mem)]
+    ys = [torch.empty_like(x) for x in xs]
+    with pytest.raises(pg.PieError) as ei:
+        grp.apply(xs, ys)
+    assert ei.value.code == 1
+    mem[1].profile_end()

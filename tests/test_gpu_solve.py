@@ -66,3 +66,23 @@ def test_solve_rejects_fp32_and_handles_zero_rhs(pg):
     pr = pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=2.0)
     x, st = pr.solve(torch.zeros(pr.N, dtype=torch.complex128, device="cuda"))
     assert st["converged"] and st["iterations"] == 0 and torch.count_nonzero(x).item() == 0
+
+
+def test_solver_error_paths(pg):
+    """Failures are reported as status codes with the context intact: a NaN
+    right-hand side gives PIE_ERR_NAN, an unreachable tolerance
+    PIE_ERR_NOCONV (returned as converged=False), and the problem keeps
+    working afterwards."""
+    import torch
+    xyz, tri = pi.icosphere(2)
+    pr = pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=2.0)
+    b = pr.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
+    bn = b.clone()
+    bn[3] = float("nan")
+    with pytest.raises(pg.PieError) as ei:
+        pr.solve(bn)
+    assert ei.value.code == 10
+    x, st = pr.solve(b, tol=1e-14, maxit=50, restart=20)
+    assert not st["converged"] and st["iterations"] == 50
+    x, st = pr.solve(b, tol=1e-5)
+    assert st["converged"]
