@@ -174,6 +174,20 @@ pie_status pie_apply_t(pie_problem* pr, const void* x, void* y, int nrhs, int dt
  * as a sparse preconditioner and for checking the near part by itself. */
 pie_status pie_apply_near(pie_problem* pr, const void* x, void* y, int nrhs, int dtype, void* stream);
 
+/* The product split by where its interactions run (Section 3).  Every
+ * triangle pair (t, s) -- boxes by centroid -- is either near (neighbouring
+ * leaf boxes) or translated at exactly one level l in [3, L]: the level at
+ * which the ancestor boxes of t and s stop being neighbours (their parents
+ * are neighbours).  y = near * Z_near x + sum of Z_l x over the levels l
+ * whose bit (1u << l) is set in level_mask; level_mask = 0xFFFFFFFF with
+ * near = 1 is pie_apply, and the parts sum to it up to the far part's
+ * rounding.  For per-level error checks against exact pair sums: after the
+ * call, pie_problem_stage(pr, 3, ...) holds the per-triangle potentials of
+ * the far part alone.  One right-hand side (x, y: device, N complex of the
+ * problem's dtype).  Errors: PIE_ERR_PARAM, PIE_ERR_CUDA. */
+pie_status pie_apply_levels(pie_problem* pr, const void* x, void* y, uint32_t level_mask, int near, int dtype,
+                            void* stream);
+
 /* Allocation-free variant of pie_apply_near (the paper has no counterpart:
  * this serves callers that cannot allocate device memory when they need a
  * product -- code inside a CUDA-graph capture they do not own, hosts that
@@ -210,7 +224,8 @@ pie_status pie_profile_end(pie_problem* pr, double* stage_ms, int32_t* applies);
  * (after aggregation / interpolation), which = 1 incoming patterns G_l (after
  * translation and anterpolation), 2 = per-triangle local coefficients
  * [T][6] (a, beta_x, beta_y, beta_z, sigma, d) in tree order (level ignored),
- * 3 = per-triangle potentials [T][6] (U, V_x, V_y, V_z, T1, T2), 4 = near
+ * 3 = per-triangle potentials [T][6] (U, V_x, V_y, V_z, T1, T2) of the far
+ * part (of the near part after pie_apply_near), 4 = near
  * pair moments [8][nnz] (m0, mt_xyz, ms_xyz, mts; entries ordered by test
  * triangle in tree order, then by near box, then by source triangle),
  * 5 = leaf radiation table Pi [T][P/2], 6 = leaf radiation table M

@@ -161,8 +161,9 @@ class MLFMA:
         tr = self.tree
         return np.add.reduceat(contrib, tr.leaf_start[:-1], axis=0)
 
-    def far_patterns(self, coef):
-        """Stage outputs: S[l] radiated patterns and G[l] incoming patterns."""
+    def far_patterns(self, coef, levels=None):
+        """Stage outputs: S[l] radiated patterns and G[l] incoming patterns.
+        ``levels`` (optional) keeps the translations of those levels only."""
         tr, L = self.tree, self.L
         S = {L: self.aggregate(coef)}
         for l in range(L - 1, 2, -1):
@@ -177,7 +178,8 @@ class MLFMA:
             ptr, src, off = tr.il_ptr[l], tr.il_idx[l], tr.il_off[l]
             dst = np.repeat(np.arange(tr.keys[l].size), np.diff(ptr))
             Gl = np.zeros_like(S[l])
-            np.add.at(Gl, dst, self.trans[l][off][:, None, :] * S[l][src])
+            if levels is None or l in levels:
+                np.add.at(Gl, dst, self.trans[l][off][:, None, :] * S[l][src])
             G[l] = Gl
         for l in range(3, L):
             octs = tr.keys[l + 1] & 7
@@ -213,7 +215,9 @@ class MLFMA:
             y[E + t] += T2[i]
         return y
 
-    def apply(self, x, near=True, far=True, stages=False):
+    def apply(self, x, near=True, far=True, stages=False, levels=None):
+        """y = Z x; near / far switch the two parts, ``levels`` keeps the
+        translations of those tree levels only (oracle.levels)."""
         coef = self.coefficients(x)
         T = coef[0].size
         pots = [np.zeros(T, np.complex128), np.zeros((T, 3), np.complex128),
@@ -222,7 +226,7 @@ class MLFMA:
         if near:
             pots = [p + q for p, q in zip(pots, self.near_potentials(coef))]
         if far:
-            S, G = self.far_patterns(coef)
+            S, G = self.far_patterns(coef, levels)
             pots = [p + q for p, q in zip(pots, self.disaggregate(G[self.L]))]
         y = self.assemble(pots)
         if stages:

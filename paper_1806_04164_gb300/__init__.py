@@ -61,7 +61,8 @@ EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_
            "pie_farfield", "pie_solve", "pie_profile_begin", "pie_profile_end", "pie_apply_near_noalloc", "pie_apply_t",
            "pie_farfield_adjoint", "pie_apply_single_layer", "pie_solve_single_layer", "pie_rhs_potential",
            "pie_nearfield", "pie_problem_get_tuning", "pie_problem_set_tuning", "pie_problem_autotune",
-           "pie_tune_levels", "pie_group_create", "pie_group_apply", "pie_group_info", "pie_group_destroy"]
+           "pie_tune_levels", "pie_group_create", "pie_group_apply", "pie_group_info", "pie_group_destroy",
+           "pie_apply_levels"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -104,6 +105,7 @@ def lib():
         L.pie_profile_begin.argtypes = [vp, i32]
         L.pie_profile_end.argtypes = [vp, PD, P32]
         L.pie_solve.argtypes = [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
+        L.pie_apply_levels.argtypes = [vp, vp, vp, ctypes.c_uint32, i32, i32, vp]
         PT = ctypes.POINTER(Tuning)
         L.pie_problem_get_tuning.argtypes = [vp, PT]
         L.pie_problem_set_tuning.argtypes = [vp, PT]
@@ -236,6 +238,21 @@ class Problem:
         fn = lib().pie_apply_near if near_only else lib().pie_apply
         _check(fn(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), nrhs,
                   self.dtype_code, _stream(stream)))
+        return y
+
+    def apply_levels(self, x, levels, near=False, y=None, stream=None):
+        """y = [Z_near x] + sum over `levels` of Z_l x (pie_apply_levels): the
+        part of the product translated at the given tree levels."""
+        import torch
+        x = _dense(x)
+        assert x.is_cuda and x.dtype == self.torch_dtype and x.dim() == 1 and x.shape[0] == self.N
+        if y is None:
+            y = torch.empty_like(x)
+        mask = 0
+        for l in levels:
+            mask |= 1 << int(l)
+        _check(lib().pie_apply_levels(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                      mask, 1 if near else 0, self.dtype_code, _stream(stream)))
         return y
 
     def profile_begin(self, max_applies):

@@ -240,6 +240,25 @@ pie_status pie_apply(pie_problem* h, const void* x, void* y, int nrhs, int dtype
   return apply_api(h, x, y, nrhs, dtype, stream, false);
 }
 
+pie_status pie_apply_levels(pie_problem* h, const void* x, void* y, uint32_t level_mask, int near, int dtype,
+                            void* stream) {
+  if (!h || !x || !y || (near != 0 && near != 1)) {
+    set_error("pie_apply_levels: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  Problem& pr = h->p;
+  if (dtype != (pr.io_f32() ? PIE_C64 : PIE_C128)) {
+    set_error("pie_apply_levels: dtype does not match the problem precision");
+    return PIE_ERR_PARAM;
+  }
+  pr.far_mask = level_mask;
+  pr.with_near = near == 1;
+  pie_status s = apply_batch(pr, x, y, 1, static_cast<cudaStream_t>(stream));
+  pr.far_mask = 0xffffffffu;
+  pr.with_near = true;
+  return s;
+}
+
 pie_status pie_apply_near(pie_problem* h, const void* x, void* y, int nrhs, int dtype, void* stream) {
   return apply_api(h, x, y, nrhs, dtype, stream, true);
 }

@@ -677,7 +677,8 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   // runs on the side stream (HBM-bound, a bounded grid) while the far part
   // (FP64-ALU-bound) runs here; per-stage profiling keeps them in order.
   const bool profiling = pr.prof_n < pr.prof_cap;
-  const bool overlap = pr.tune.overlap && !profiling;
+  const bool with_near = pr.with_near;
+  const bool overlap = pr.tune.overlap && !profiling && with_near;
   C2<Rio>* pot2 = static_cast<C2<Rio>*>(pr.pot2);
   cudaStream_t sn = st;
   unsigned near_grid = nblk(pr.T * 32, 256);
@@ -698,7 +699,9 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
         pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
         static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot2, nrhs, sT, sT);
   };
-  if (nrhs == 1)
+  if (!with_near)
+    pot2 = nullptr;
+  else if (nrhs == 1)
     near_launch(std::integral_constant<int, 1>());
   else if (nrhs == 2 || sizeof(Rm) == 8)
     near_launch(std::integral_constant<int, 2>());
@@ -743,6 +746,11 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   prof_mark(pr, 3, true, st);
   prof_mark(pr, 4, false, st);
   for (int l = 3; l <= L; ++l) {
+    if (!((pr.far_mask >> l) & 1u)) {  // level left out: no incoming pattern of its own
+      pie_status s = cuda_check(cudaMemsetAsync(pr.lev[l].G, 0, sizeof(C2<Rf>) * sl(l) * nr, st), "memset");
+      if (s != PIE_OK) return s;
+      continue;
+    }
     k_trans<Rf><<<dim3(unsigned(pr.lev[l].nb), nr), tpb, 0, st>>>(
         P, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off, static_cast<const C2<Rf>*>(pr.lev[l].trans),
         static_cast<const C2<Rf>*>(pr.lev[l].S), static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));

@@ -102,6 +102,10 @@ struct Problem {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int nsm = 0;                   // SMs of the device
   pie_tuning tune{1, 2, 1};
+  // parts of the product that run (pie_apply_levels): translations at the
+  // levels whose bit is set, and the near part
+  uint32_t far_mask = 0xffffffffu;
+  bool with_near = true;
 
   bool near_f32() const { return par.precision != PIE_FP64; }
   bool far_f32() const { return par.precision == PIE_FP32; }
