@@ -30,6 +30,10 @@ WORKLOAD = dict(workload="pec_sphere_icosphere7_1M", mesh="icosphere n=7, R=1 m"
 METRIC = "PIE MLFMA matvecs/s (1M unk)"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 FALLBACK_HBM_GBS = 6800.0
+# DRAM read + write bytes per algorithmic flop of a stage's kernels, from one
+# ncu capture (profiles/product_kernels_icosphere6.md); valid while those
+# kernels are unchanged
+NCU_BYTES_PER_FLOP = {"translation": 78.2e6 / 1.3376e9}
 
 
 def parse():
@@ -284,9 +288,12 @@ def run_ours(args):
                 "frac": achieved / hbm, "peak_source": hbm_src, "algorithmic_bytes": amount, "traffic": None}
     else:
         achieved = amount / (per_launch_ms * 1e-3) / 1e12
+        traffic = NCU_BYTES_PER_FLOP[dom] * amount if dom in NCU_BYTES_PER_FLOP else None
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal FP64",
-                "algorithmic_flops": amount, "traffic": None}
+                "algorithmic_flops": amount, "traffic": traffic,
+                "traffic_source": ("ncu dram bytes per flop on the 81,920-triangle sphere, scaled by flops "
+                                   "(profiles/product_kernels_icosphere6.md)") if traffic else None}
     stage_share = {k: round(v / sum(main["stage_ms"].values()), 4) for k, v in main["stage_ms"].items()}
     fp = results["fp64"]
     line = {

@@ -234,56 +234,136 @@ __global__ void k_interp(int P, const int32_t* __restrict__ child_start, const i
 //   shat[i'][m] = sum_j e^{-i m phi_j} s[i'][j],  K_m = (1/NPHI) DFT_d f_ii'(d).
 // F^T uses K_m transposed.
 
-__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
-__host__ __device__ constexpr int bitrev(int x, int bits) {
-  int r = 0;
-  for (int b = 0; b < bits; ++b) r |= ((x >> b) & 1) << (bits - 1 - b);
-  return r;
+// Structure used below (N_theta = 8, so NPHI = 16 and degrees up to 7):
+//  * K_m = K_{-m}, and K_8 = 0: azimuthal order |m| <= degree <= 7, so the
+//    Nyquist frequency m = 8 carries nothing;
+//  * the Gauss-Legendre theta nodes are symmetric about the equator and
+//    P_l^m(-x) = (-1)^(l+m) P_l^m(x), so every K_m commutes with the row
+//    reflection i -> NT-1-i.  In the sums and differences of mirrored rows,
+//    se_k = s_k + s_{NT-1-k}, so_k = s_k - s_{NT-1-k} (k < NT/2), K_m is two
+//    (NT/2) x (NT/2) blocks:  y_i = ye_i + yo_i, y_{NT-1-i} = ye_i - yo_i with
+//    ye = KE se, yo = KO so, KE_ik = (K_ik + K_i,NT-1-k)/2,
+//    KO_ik = (K_ik - K_i,NT-1-k)/2.  Half the multiply-adds of the full block.
+
+// 4-point DFT in place, X_k = sum_n x_n w^(nk), w = -i (forward) or +i.
+template <bool INV, typename R>
+__device__ __forceinline__ void dft4(C2<R>& a, C2<R>& b, C2<R>& c, C2<R>& d) {
+  const C2<R> t0 = mk<R>(a.x + c.x, a.y + c.y), t1 = mk<R>(a.x - c.x, a.y - c.y);
+  const C2<R> t2 = mk<R>(b.x + d.x, b.y + d.y), t3 = mk<R>(b.x - d.x, b.y - d.y);
+  a = mk<R>(t0.x + t2.x, t0.y + t2.y);
+  c = mk<R>(t0.x - t2.x, t0.y - t2.y);
+  // forward: X1 = t1 - i t3, X3 = t1 + i t3 (inverse: signs swapped)
+  const C2<R> p = mk<R>(t1.x + t3.y, t1.y - t3.x), q = mk<R>(t1.x - t3.y, t1.y + t3.x);
+  b = INV ? q : p;
+  d = INV ? p : q;
 }
 
-// In-register radix-2 FFT; tw[k] = exp(-2 pi i k / N), k < N/2.  Forward
-// uses tw, inverse its conjugate (no 1/N scaling).
-template <int N, typename R>
-__device__ __forceinline__ void fft_reg(C2<R>* x, const C2<R>* tw, bool inverse) {
-  constexpr int LG = ilog2c(N);
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const int j = bitrev(i, LG);
-    if (j > i) {
-      C2<R> t = x[i];
-      x[i] = x[j];
-      x[j] = t;
-    }
+// v * exp(-/+ 2 pi i E / 16) for the exponents of the 16 = 4 x 4 split.
+// cos(pi/8) = sqrt(2 + sqrt 2) / 2, sin(pi/8) = sqrt(2 - sqrt 2) / 2.
+template <bool INV, int E, typename R>
+__device__ __forceinline__ C2<R> twiddle16(C2<R> v) {
+  constexpr double c8 = 0.92387953251128675613, s8 = 0.38268343236508977173, h = 0.70710678118654752440;
+  constexpr double c = E == 1 ? c8 : E == 3 ? s8 : E == 9 ? -c8 : 0.0;
+  constexpr double s = E == 1 ? s8 : E == 3 ? c8 : E == 9 ? -s8 : 0.0;
+  const R x = v.x, y = v.y;
+  if constexpr (E == 2) {  // (1 -/+ i) h
+    return INV ? mk<R>(R(h) * (x - y), R(h) * (x + y)) : mk<R>(R(h) * (x + y), R(h) * (y - x));
+  } else if constexpr (E == 4) {  // -/+ i
+    return INV ? mk<R>(-y, x) : mk<R>(y, -x);
+  } else if constexpr (E == 6) {  // (-1 -/+ i) h
+    return INV ? mk<R>(-R(h) * (x + y), R(h) * (x - y)) : mk<R>(R(h) * (y - x), -R(h) * (x + y));
+  } else {  // c -/+ i s
+    return INV ? mk<R>(fma(x, R(c), -y * R(s)), fma(y, R(c), x * R(s)))
+               : mk<R>(fma(x, R(c), y * R(s)), fma(y, R(c), -x * R(s)));
   }
+}
+
+// 16-point DFT in registers, X_k = sum_n x_n exp(-/+ 2 pi i n k / 16) (no
+// scaling): n = 4 q + r, k = k1 + 4 k2; 4-point DFTs over q, twiddles
+// exp(-/+ 2 pi i r k1 / 16), 4-point DFTs over r.  X is returned in out.
+template <bool INV, typename R>
+__device__ __forceinline__ void fft16(C2<R>* x, C2<R>* out) {
 #pragma unroll
-  for (int len = 2; len <= N; len <<= 1) {
-    const int half = len >> 1, step = N / len;
+  for (int r = 0; r < 4; ++r) dft4<INV>(x[r], x[r + 4], x[r + 8], x[r + 12]);  // x[r + 4 k1] = Y_r[k1]
+  x[5] = twiddle16<INV, 1>(x[5]);
+  x[9] = twiddle16<INV, 2>(x[9]);
+  x[13] = twiddle16<INV, 3>(x[13]);
+  x[6] = twiddle16<INV, 2>(x[6]);
+  x[10] = twiddle16<INV, 4>(x[10]);
+  x[14] = twiddle16<INV, 6>(x[14]);
+  x[7] = twiddle16<INV, 3>(x[7]);
+  x[11] = twiddle16<INV, 6>(x[11]);
+  x[15] = twiddle16<INV, 9>(x[15]);
 #pragma unroll
-    for (int i = 0; i < N; i += len) {
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
 #pragma unroll
-      for (int k = 0; k < half; ++k) {
-        C2<R> w = tw[k * step];
-        if (inverse) w.y = -w.y;
-        C2<R> u = x[i + k], v = cmul(x[i + k + half], w);
-        x[i + k] = mk<R>(u.x + v.x, u.y + v.y);
-        x[i + k + half] = mk<R>(u.x - v.x, u.y - v.y);
-      }
-    }
-  }
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) out[k1 + 4 * k2] = x[4 * k1 + k2];
 }
 
 constexpr int kFftBatch = 4;  // children per batch in the factorised filter kernels
 
+// Mirror-split blocks of K_m (or of K_m^T when TR) in shared memory:
+// KE[m][i][k], KO[m][i][k], i, k < NT/2.
+template <int NT, bool TR, typename Rf>
+__device__ __forceinline__ void load_split_blocks(const Rf* __restrict__ Kf, Rf* KE, Rf* KO, int tid, int nth) {
+  constexpr int NPHI = 2 * NT, H = NT / 2;
+  for (int it = tid; it < NPHI * H * H; it += nth) {
+    const int m = it / (H * H), i = (it / H) % H, k = it % H;
+    const Rf* Km = Kf + m * NT * NT;
+    const Rf a = TR ? Km[k * NT + i] : Km[i * NT + k];
+    const Rf b = TR ? Km[(NT - 1 - k) * NT + i] : Km[i * NT + NT - 1 - k];
+    KE[it] = Rf(0.5) * (a + b);
+    KO[it] = Rf(0.5) * (a - b);
+  }
+}
+
+// One azimuthal frequency m of one (child, component): y = K_m a over the NT
+// theta rows (a strided by one in shared memory), written to out[i * BP].
+template <int NT, int BP, typename Rf>
+__device__ __forceinline__ void apply_split_block(const C2<Rf>* a, const Rf* KE, const Rf* KO, C2<Rf>* out) {
+  constexpr int H = NT / 2;
+  C2<Rf> se[H], so[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const C2<Rf> u = a[k], v = a[NT - 1 - k];
+    se[k] = mk<Rf>(u.x + v.x, u.y + v.y);
+    so[k] = mk<Rf>(u.x - v.x, u.y - v.y);
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    C2<Rf> ye = mk<Rf>(0, 0), yo = mk<Rf>(0, 0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      rfma(ye, KE[i * H + k], se[k]);
+      rfma(yo, KO[i * H + k], so[k]);
+    }
+    out[i * BP] = mk<Rf>(ye.x + yo.x, ye.y + yo.y);
+    out[(NT - 1 - i) * BP] = mk<Rf>(ye.x - yo.x, ye.y - yo.y);
+  }
+}
+
+template <int NT, typename Rf>
+__host__ __device__ constexpr size_t fft_smem_bytes(bool interp) {
+  constexpr int NPHI = 2 * NT, P = NT * NPHI;
+  return sizeof(C2<Rf>) * (size_t(kFftBatch) * kComp * NPHI * (NT + 1) + size_t(kFftBatch) * kComp * NT * (NPHI + 1) +
+                           (interp ? size_t(kComp) * P : 0)) +
+         sizeof(Rf) * 2 * NPHI * (NT / 2) * (NT / 2);
+}
+
 // a3 (factorised): one block per parent box, kFftBatch children at a time,
-// one thread per (child, component, theta row).
+// one thread per (child, component, theta row) for the DFTs and per (child,
+// component, azimuthal frequency) for the K_m blocks.
 template <int NT, typename Rf>
 __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
     const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Sc,
     const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Sp, int64_t sSc = 0,
     int64_t sSp = 0) {
+  static_assert(NT == 8, "the register DFT is the 16-point one");
   Sc += blockIdx.y * sSc;
   Sp += blockIdx.y * sSp;
-  constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch;
+  constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch, H = NT / 2;
   // rows padded by one element (AP, BP) so that lanes striding over rows hit
   // distinct shared-memory banks
   constexpr int AP = NT + 1, BP = NPHI + 1;
@@ -291,16 +371,11 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
   C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);  // spectra [slot][c][m][i (AP)], then results [slot][c][i][j (BP)]
   C2<Rf>* B = A + NB * kComp * NPHI * AP;             // filtered spectra [slot][c][i][m (BP)]
   C2<Rf>* acc = B + NB * kComp * NT * BP;             // parent pattern [c][p]
-  C2<Rf>* tw = acc + kComp * P;                       // twiddles
-  Rf* K = reinterpret_cast<Rf*>(tw + NPHI / 2);       // K_m blocks
+  Rf* KE = reinterpret_cast<Rf*>(acc + kComp * P);    // mirror-split K_m blocks
+  Rf* KO = KE + NPHI * H * H;
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int i = tid; i < NPHI * NT * NT; i += nth) K[i] = Kf[i];
+  load_split_blocks<NT, false>(Kf, KE, KO, tid, nth);
   for (int i = tid; i < kComp * P; i += nth) acc[i] = mk<Rf>(0, 0);
-  if (tid < NPHI / 2) {
-    Rf sn, cs;
-    sincospi(Rf(2 * tid) / Rf(NPHI), &sn, &cs);
-    tw[tid] = mk<Rf>(cs, -sn);
-  }
   const int b = blockIdx.x, c0 = child_start[b], c1 = child_start[b + 1];
   for (int base = c0; base < c1; base += NB) {
     const int nb = min(NB, c1 - base);
@@ -308,41 +383,39 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
     {  // forward DFT of every row
       const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
       if (slot < nb) {
-        C2<Rf> x[NPHI];
+        C2<Rf> x[NPHI], X[NPHI];
         const C2<Rf>* src = Sc + ((int64_t)(base + slot) * kComp + c) * P + i * NPHI;
 #pragma unroll
         for (int j = 0; j < NPHI; ++j) x[j] = src[j];
-        fft_reg<NPHI>(x, tw, false);
+        fft16<false>(x, X);
 #pragma unroll
-        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * AP + i] = x[m];
+        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * AP + i] = X[m];
       }
     }
     __syncthreads();
-    for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // K_m blocks
+    for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // K_m blocks (K_8 = 0)
       const int sc = it / NPHI, m = it % NPHI;
-      const C2<Rf>* a = A + (sc * NPHI + m) * AP;
-      const Rf* Km = K + m * NT * NT;
+      C2<Rf>* out = B + sc * NT * BP + m;
+      if (m == NPHI / 2) {
 #pragma unroll
-      for (int i = 0; i < NT; ++i) {
-        C2<Rf> t = mk<Rf>(0, 0);
-#pragma unroll
-        for (int k = 0; k < NT; ++k) rfma(t, Km[i * NT + k], a[k]);
-        B[(sc * NT + i) * BP + m] = t;
+        for (int i = 0; i < NT; ++i) out[i * BP] = mk<Rf>(0, 0);
+      } else {
+        apply_split_block<NT, BP>(A + (sc * NPHI + m) * AP, KE + m * H * H, KO + m * H * H, out);
       }
     }
     __syncthreads();
     {  // inverse DFT, phase shift to the parent centre
       const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
       if (slot < nb) {
-        C2<Rf> x[NPHI];
+        C2<Rf> x[NPHI], X[NPHI];
         const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * BP;
 #pragma unroll
         for (int m = 0; m < NPHI; ++m) x[m] = src[m];
-        fft_reg<NPHI>(x, tw, true);
+        fft16<true>(x, X);
         const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
         C2<Rf>* dst = A + ((slot * kComp + c) * NT + i) * BP;
 #pragma unroll
-        for (int j = 0; j < NPHI; ++j) dst[j] = cmul(ph[j], x[j]);
+        for (int j = 0; j < NPHI; ++j) dst[j] = cmul(ph[j], X[j]);
       }
     }
     __syncthreads();
@@ -368,22 +441,18 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
     const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Gp,
     const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Gc, int64_t sGp = 0,
     int64_t sGc = 0) {
+  static_assert(NT == 8, "the register DFT is the 16-point one");
   Gp += blockIdx.y * sGp;
   Gc += blockIdx.y * sGc;
-  constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch;
+  constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch, H = NT / 2;
   constexpr int AP = NT + 1, BP = NPHI + 1;  // padded rows (bank spreading)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);
   C2<Rf>* B = A + NB * kComp * NPHI * AP;
-  C2<Rf>* tw = B + NB * kComp * NT * BP;
-  Rf* K = reinterpret_cast<Rf*>(tw + NPHI / 2);
+  Rf* KE = reinterpret_cast<Rf*>(B + NB * kComp * NT * BP);
+  Rf* KO = KE + NPHI * H * H;
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int i = tid; i < NPHI * NT * NT; i += nth) K[i] = Kf[i];
-  if (tid < NPHI / 2) {
-    Rf sn, cs;
-    sincospi(Rf(2 * tid) / Rf(NPHI), &sn, &cs);
-    tw[tid] = mk<Rf>(cs, -sn);
-  }
+  load_split_blocks<NT, true>(Kf, KE, KO, tid, nth);
   const int b = blockIdx.x, c0 = child_start[b], c1 = child_start[b + 1];
   for (int base = c0; base < c1; base += NB) {
     const int nb = min(NB, c1 - base);
@@ -391,7 +460,7 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
     {
       const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
       if (slot < nb) {
-        C2<Rf> x[NPHI];
+        C2<Rf> x[NPHI], X[NPHI];
         const C2<Rf>* src = Gp + ((int64_t)b * kComp + c) * P + i * NPHI;
         const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
 #pragma unroll
@@ -399,38 +468,36 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
           C2<Rf> g = src[j], w = ph[j];
           x[j] = mk<Rf>(w.x * g.x + w.y * g.y, w.x * g.y - w.y * g.x);  // conj(w) g
         }
-        fft_reg<NPHI>(x, tw, false);
+        fft16<false>(x, X);
 #pragma unroll
-        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * AP + i] = x[m];
+        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * AP + i] = X[m];
       }
     }
     __syncthreads();
-    for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // transposed K_m blocks
+    for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // transposed K_m blocks (K_8 = 0)
       const int sc = it / NPHI, m = it % NPHI;
-      const C2<Rf>* a = A + (sc * NPHI + m) * AP;
-      const Rf* Km = K + m * NT * NT;
+      C2<Rf>* out = B + sc * NT * BP + m;
+      if (m == NPHI / 2) {
 #pragma unroll
-      for (int i = 0; i < NT; ++i) {
-        C2<Rf> t = mk<Rf>(0, 0);
-#pragma unroll
-        for (int k = 0; k < NT; ++k) rfma(t, Km[k * NT + i], a[k]);
-        B[(sc * NT + i) * BP + m] = t;
+        for (int i = 0; i < NT; ++i) out[i * BP] = mk<Rf>(0, 0);
+      } else {
+        apply_split_block<NT, BP>(A + (sc * NPHI + m) * AP, KE + m * H * H, KO + m * H * H, out);
       }
     }
     __syncthreads();
     {
       const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
       if (slot < nb) {
-        C2<Rf> x[NPHI];
+        C2<Rf> x[NPHI], X[NPHI];
         const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * BP;
 #pragma unroll
         for (int m = 0; m < NPHI; ++m) x[m] = src[m];
-        fft_reg<NPHI>(x, tw, true);
+        fft16<true>(x, X);
         C2<Rf>* dst = Gc + ((int64_t)(base + slot) * kComp + c) * P + i * NPHI;
 #pragma unroll
         for (int j = 0; j < NPHI; ++j) {
           C2<Rf> g = dst[j];
-          dst[j] = mk<Rf>(g.x + x[j].x, g.y + x[j].y);
+          dst[j] = mk<Rf>(g.x + X[j].x, g.y + X[j].y);
         }
       }
     }
@@ -633,10 +700,7 @@ void prof_mark(Problem& pr, int stage, bool end, cudaStream_t st) {
 
 template <int NT, typename Rf>
 static size_t fft_smem(bool interp) {
-  constexpr int NPHI = 2 * NT, P = NT * NPHI;
-  return sizeof(C2<Rf>) * (kFftBatch * kComp * NPHI * (NT + 1) + kFftBatch * kComp * NT * (NPHI + 1) +
-                           (interp ? kComp * P : 0) + NPHI / 2) +
-         sizeof(Rf) * NPHI * NT * NT;
+  return fft_smem_bytes<NT, Rf>(interp);
 }
 
 // Opt the factorised filter kernels into their (above 48 KB) dynamic shared memory.
