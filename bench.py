@@ -39,7 +39,7 @@ NCU_BYTES_PER_FLOP = {"translation": 78.2e6 / 1.3376e9}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-rows", type=int, default=4, help="rows of the dense oracle product for the CPU baseline")
@@ -70,7 +70,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region: the sampler is started and its first sample awaited before the
+    region opens, and only samples taken between start() and stop() count."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -78,30 +80,51 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.p = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append((time.time(), line))
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return self
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+        t = time.time()
+        while not self.lines and time.time() - t < 5.0:
+            time.sleep(0.02)
         return self
 
+    def start(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        self.t1 = time.time()
+
     def __exit__(self, *a):
-        self.out = ""
         if self.p is not None:
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.p.kill()
-                self.out, _ = self.p.communicate()
+            self.th.join(timeout=5)
 
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in (self.out or "").strip().splitlines():
+        t0 = self.t0 if self.t0 is not None else -1e300
+        t1 = self.t1 if self.t1 is not None else 1e300
+        for ts, line in self.lines:
+            if ts < t0 or ts > t1 + 0.1:
+                continue
             f = [x.strip() for x in line.split(",")]
             if len(f) < 8:
                 continue
@@ -202,11 +225,13 @@ def run_ours(args):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             torch.cuda.synchronize()
+            clk.start()
             ev0.record(stream)
             for _ in range(args.steps):
                 pr.apply(x, y)
             ev1.record(stream)
             torch.cuda.synchronize()
+            clk.stop()
         barrier()
         ms = ev0.elapsed_time(ev1)
         ms_max = max_over_ranks(ms)
@@ -359,6 +384,7 @@ def multimesh_run(args, stream, barrier, max_over_ranks):
     import paper_1806_04164_gb300 as pg
     import pie_inputs as pi
     k0, nrhs = 1e-2, 64
+    steps = min(args.steps, 20)  # one launch is 4 x 64 products (~0.15 s)
     th = (np.arange(4) + 0.5) * np.pi / 4
     ph = np.arange(8) * 2 * np.pi / 8
     waves = []
@@ -393,23 +419,23 @@ def multimesh_run(args, stream, barrier, max_over_ranks):
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         grp.apply(xs, ys)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1)) / steps
     # the same products issued member after member on one stream, for contrast
     for pr, x, y in zip(members, xs, ys):
         pr.apply(x, y)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         for pr, x, y in zip(members, xs, ys):
             pr.apply(x, y)
     e1.record(stream)
     torch.cuda.synchronize()
-    seq_ms = e0.elapsed_time(e1) / args.steps
+    seq_ms = e0.elapsed_time(e1) / steps
     g = grp.info()
     out = {"value": len(members) * nrhs / (ms * 1e-3), "unit": "matvecs/s (one mesh, one right-hand side each)",
            "unknown_matvecs_per_s": sum(m.N for m in members) * nrhs / (ms * 1e-3),
@@ -436,6 +462,7 @@ def run_large(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     stream = torch.cuda.current_stream()
     k0, n = 1e-4, 8
+    steps = min(args.steps, 10)
     xyz, tri = pi.icosphere(n)
     mesh = pg.Mesh(xyz, tri)
     t0 = time.time()
@@ -459,11 +486,11 @@ def run_large(args):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 pr.apply(X[:cols], Y[:cols])
             e1.record(stream)
             torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
+            ms = e0.elapsed_time(e1) / steps
             res[f"nrhs{cols}"] = {"ms_per_pass": ms, "matvecs_per_s": cols / (ms * 1e-3)}
         del X, Y
         res["gmres"] = gmres_run(pr, args.gmres_tol, k0, noop, lambda v: v)

@@ -242,11 +242,25 @@ pie_status pie_problem_stage(pie_problem* pr, int which, int level, double* out,
 pie_status pie_rhs_planewave(pie_problem* pr, const double khat[3], const double pol[3], double E0,
                              void* b, int dtype, void* stream);
 
+/* The problem's quadrature points (Section 2: the Galerkin integrals over
+ * each triangle use a 7-point degree-5 rule): pts [T][7][3] and weights
+ * (area included) wts [T][7], host, mesh order; either may be NULL.  Where
+ * a caller evaluates its own incident potentials for pie_rhs_potentials. */
+pie_status pie_problem_quadrature(const pie_problem* pr, double* pts, double* wts);
+
+/* Right-hand side for any incident potentials (Eqs. (1)-(2)): A^inc and
+ * Phi^inc given at the points of pie_problem_quadrature, A_q [T][7][3] and
+ * Phi_q [T][7] (device, complex double, mesh order).  b_J = -<f_m, A^inc>,
+ * b_sigma = -i w eps0 <p_t, Phi^inc>, with the same rule as the operator.
+ * b: device, N complex of the problem's dtype.  Errors: PIE_ERR_PARAM. */
+pie_status pie_rhs_potentials(pie_problem* pr, const void* A_q, const void* Phi_q, void* b, int dtype,
+                              void* stream);
+
 /* Far-zone field from J (Section 2): E[d] = i w mu0/(4 pi) (I - rr) .
  * int J exp(-i k0 r.r') dr' (factor exp(i k0 r)/r removed).  rhat: host
- * ndir x 3; E: device ndir x 3 complex double.  x: device solution
- * (problem dtype). */
-pie_status pie_farfield(pie_problem* pr, const void* x, const double* rhat, int64_t ndir, void* E,
+ * ndir x 3; x: device solutions, N x nrhs (problem dtype, column j at
+ * offset j*N); E: device nrhs x ndir x 3 complex double. */
+pie_status pie_farfield(pie_problem* pr, const void* x, const double* rhat, int64_t ndir, void* E, int nrhs,
                         void* stream);
 
 /* Adjoint of the far-field map of pie_farfield: u = F^H E for E (device,
@@ -265,10 +279,15 @@ pie_status pie_farfield_adjoint(pie_problem* pr, const double* rhat, int64_t ndi
  * double; PIE_MIXED problems keep it in complex float, with the solution and
  * the true residual in complex double recomputed at every restart (iterative
  * refinement with a GMRES inner solver), so the basis precision limits the
- * progress of a cycle, not the accuracy reached.  b, x: device, N complex
- * double.  Synchronises the stream.  Errors: PIE_ERR_PARAM (PIE_FP32
- * problem), PIE_ERR_NOCONV, PIE_ERR_BREAKDOWN, PIE_ERR_NAN, PIE_ERR_CUDA. */
-pie_status pie_solve(pie_problem* pr, const void* b, void* x, double tol, int maxit, int restart,
+ * progress of a cycle, not the accuracy reached.  b, x: device, N x nrhs
+ * complex double (column j at offset j*N), solved column after column;
+ * stats: nrhs entries (host, may be NULL).  Synchronises the stream.
+ * Returns PIE_OK when every column converged, else PIE_ERR_NOCONV or
+ * PIE_ERR_BREAKDOWN of the first column that did not (the other columns are
+ * still solved); PIE_ERR_PARAM (PIE_FP32 problem), PIE_ERR_NAN and
+ * PIE_ERR_CUDA stop at once.  There is no wall-clock limit: maxit bounds
+ * the work. */
+pie_status pie_solve(pie_problem* pr, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
                      pie_solve_stats* stats, void* stream);
 
 /* Near-zone fields (Section 2).  The far zone needs J only; near-zone E needs

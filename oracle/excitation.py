@@ -34,12 +34,25 @@ def potentials(r, k0, khat, pol, E0=1.0):
     return A, Phi
 
 
+def quadrature_points(top: Topology):
+    """Points [T,7,3] and weights [T,7] (area included) of the 7-point rule."""
+    b7, w7 = radon7()
+    return physical_points(top.xyz, top.tri, b7), w7[None, :] * top.area[:, None]
+
+
 def rhs_planewave(top: Topology, k0, khat, pol, E0=1.0):
     """b in mesh order [E ; T] (complex128)."""
-    b7, w7 = radon7()
-    P = physical_points(top.xyz, top.tri, b7)           # [T,7,3]
-    W = w7[None, :] * top.area[:, None]
+    P, _ = quadrature_points(top)
     A, Phi = potentials(P, k0, khat, pol, E0)
+    return rhs_from_potentials(top, k0, A, Phi)
+
+
+def rhs_from_potentials(top: Topology, k0, A, Phi):
+    """b in mesh order for incident potentials given at the quadrature points
+    of quadrature_points: A [T,7,3], Phi [T,7]."""
+    P, W = quadrature_points(top)
+    A = np.asarray(A, np.complex128)
+    Phi = np.asarray(Phi, np.complex128)
     w = C.omega_of_k(k0)
     b = np.zeros(top.N, np.complex128)
     b[top.E:] = -1j * w * C.EPS0 * np.sum(W * Phi, axis=1)

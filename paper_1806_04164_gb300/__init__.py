@@ -62,7 +62,7 @@ EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_
            "pie_farfield_adjoint", "pie_apply_single_layer", "pie_solve_single_layer", "pie_rhs_potential",
            "pie_nearfield", "pie_problem_get_tuning", "pie_problem_set_tuning", "pie_problem_autotune",
            "pie_tune_levels", "pie_group_create", "pie_group_apply", "pie_group_info", "pie_group_destroy",
-           "pie_apply_levels"]
+           "pie_apply_levels", "pie_problem_quadrature", "pie_rhs_potentials"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -101,10 +101,12 @@ def lib():
         L.pie_nearfield.argtypes = [vp, vp, vp, PD, i64, vp, vp]
         L.pie_problem_stage.argtypes = [vp, i32, i32, PD, vp]
         L.pie_rhs_planewave.argtypes = [vp, PD, PD, dbl, vp, i32, vp]
-        L.pie_farfield.argtypes = [vp, vp, PD, i64, vp, vp]
+        L.pie_farfield.argtypes = [vp, vp, PD, i64, vp, i32, vp]
+        L.pie_problem_quadrature.argtypes = [vp, PD, PD]
+        L.pie_rhs_potentials.argtypes = [vp, vp, vp, vp, i32, vp]
         L.pie_profile_begin.argtypes = [vp, i32]
         L.pie_profile_end.argtypes = [vp, PD, P32]
-        L.pie_solve.argtypes = [vp, vp, vp, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
+        L.pie_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
         L.pie_apply_levels.argtypes = [vp, vp, vp, ctypes.c_uint32, i32, i32, vp]
         PT = ctypes.POINTER(Tuning)
         L.pie_problem_get_tuning.argtypes = [vp, PT]
@@ -362,27 +364,58 @@ class Problem:
                                        ctypes.c_void_p(b.data_ptr()), self.dtype_code, _stream(stream)))
         return b
 
+    def quadrature(self):
+        """Quadrature points [T, 7, 3] and weights [T, 7] of every triangle
+        (mesh order; pie_problem_quadrature)."""
+        pts = np.zeros((self.T, 7, 3), np.float64)
+        wts = np.zeros((self.T, 7), np.float64)
+        _check(lib().pie_problem_quadrature(self.handle, _ptr(pts, ctypes.c_double), _ptr(wts, ctypes.c_double)))
+        return pts, wts
+
+    def rhs_potentials(self, A_q, Phi_q, stream=None):
+        """Right-hand side for incident potentials given at the quadrature
+        points: A_q [T, 7, 3], Phi_q [T, 7] complex128 device tensors
+        (pie_rhs_potentials)."""
+        import torch
+        A_q, Phi_q = _dense(A_q), _dense(Phi_q)
+        assert A_q.is_cuda and Phi_q.is_cuda and A_q.dtype == torch.complex128 and Phi_q.dtype == torch.complex128
+        assert A_q.shape == (self.T, 7, 3) and Phi_q.shape == (self.T, 7)
+        b = torch.empty(self.N, dtype=self.torch_dtype, device="cuda")
+        _check(lib().pie_rhs_potentials(self.handle, ctypes.c_void_p(A_q.data_ptr()), ctypes.c_void_p(Phi_q.data_ptr()),
+                                        ctypes.c_void_p(b.data_ptr()), self.dtype_code, _stream(stream)))
+        return b
+
     def farfield(self, x, rhat, stream=None):
+        """E [ndir, 3] for x [N], or [nrhs, ndir, 3] for x [nrhs, N] (pie_farfield)."""
         import torch
         rh = np.ascontiguousarray(rhat, np.float64)
         x = _dense(x)
-        E = torch.empty((rh.shape[0], 3), dtype=torch.complex128, device="cuda")
+        nrhs = 1 if x.dim() == 1 else x.shape[0]
+        shape = (rh.shape[0], 3) if x.dim() == 1 else (nrhs, rh.shape[0], 3)
+        E = torch.empty(shape, dtype=torch.complex128, device="cuda")
+        if nrhs == 0:
+            return E
         _check(lib().pie_farfield(self.handle, ctypes.c_void_p(x.data_ptr()), _ptr(rh, ctypes.c_double),
-                                  rh.shape[0], ctypes.c_void_p(E.data_ptr()), _stream(stream)))
+                                  rh.shape[0], ctypes.c_void_p(E.data_ptr()), nrhs, _stream(stream)))
         return E
 
     def solve(self, b, tol=1e-6, maxit=1000, restart=100, stream=None):
-        """Restarted GMRES on Z x = b (pie_solve)."""
+        """Restarted GMRES on Z x = b (pie_solve).  b [N] gives (x, stats);
+        b [nrhs, N] gives (x [nrhs, N], [stats per column])."""
         import torch
         b = _dense(b)
         x = torch.zeros_like(b)
-        st = SolveStats()
-        code = lib().pie_solve(self.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), tol,
-                               maxit, restart, ctypes.byref(st), _stream(stream))
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        st = (SolveStats * max(nrhs, 1))()
+        if nrhs == 0:
+            return x, []
+        code = lib().pie_solve(self.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, tol,
+                               maxit, restart, st, _stream(stream))
         if code not in (0, 8):
             _check(code)
-        return x, dict(iterations=st.iterations, rel_residual=st.rel_residual, seconds=st.seconds,
-                       converged=code == 0)
+        stats = [dict(iterations=s.iterations, rel_residual=s.rel_residual, seconds=s.seconds,
+                      converged=s.rel_residual <= tol) for s in st[:nrhs]]
+        return (x, stats[0]) if b.dim() == 1 else (x, stats)
 
     @property
     def tuning(self):

@@ -399,22 +399,83 @@ pie_status pie_rhs_planewave(pie_problem* h, const double khat[3], const double 
   return rhs_planewave(h->p, khat, pol, E0, b, static_cast<cudaStream_t>(stream));
 }
 
-pie_status pie_farfield(pie_problem* h, const void* x, const double* rhat, int64_t ndir, void* E, void* stream) {
-  if (!h || !x || !rhat || !E || ndir < 0) {
-    set_error("NULL argument");
+pie_status pie_farfield(pie_problem* h, const void* x, const double* rhat, int64_t ndir, void* E, int nrhs,
+                        void* stream) {
+  if (!h || !x || !rhat || !E || ndir < 0 || nrhs < 1) {
+    set_error("pie_farfield: invalid argument");
     return PIE_ERR_PARAM;
   }
   if (ndir == 0) return PIE_OK;
-  return farfield(h->p, x, rhat, ndir, E, static_cast<cudaStream_t>(stream));
+  Problem& pr = h->p;
+  const size_t col = (pr.io_f32() ? sizeof(cf) : sizeof(cd)) * size_t(pr.N);
+  for (int j = 0; j < nrhs; ++j) {
+    pie_status s = farfield(pr, static_cast<const char*>(x) + col * j, rhat, ndir,
+                            static_cast<cd*>(E) + size_t(ndir) * 3 * j, static_cast<cudaStream_t>(stream));
+    if (s != PIE_OK) return s;
+  }
+  return PIE_OK;
 }
 
-pie_status pie_solve(pie_problem* h, const void* b, void* x, double tol, int maxit, int restart,
+pie_status pie_solve(pie_problem* h, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
                      pie_solve_stats* stats, void* stream) {
-  if (!h || !b || !x || !(tol > 0) || maxit < 1 || restart < 1) {
+  if (!h || !b || !x || nrhs < 1 || !(tol > 0) || maxit < 1 || restart < 1) {
     set_error("pie_solve: invalid argument");
     return PIE_ERR_PARAM;
   }
-  return solve(h->p, b, x, tol, maxit, restart, stats, static_cast<cudaStream_t>(stream));
+  // one GMRES per column; a column that does not converge does not stop the
+  // others, a failure of the device or the arithmetic does
+  Problem& pr = h->p;
+  const size_t col = sizeof(cd) * size_t(pr.N);
+  pie_status worst = PIE_OK;
+  std::string msg;
+  for (int j = 0; j < nrhs; ++j) {
+    pie_status s = solve(pr, static_cast<const char*>(b) + col * j, static_cast<char*>(x) + col * j, tol, maxit,
+                         restart, stats ? stats + j : nullptr, static_cast<cudaStream_t>(stream));
+    if (s == PIE_ERR_NOCONV || s == PIE_ERR_BREAKDOWN) {
+      if (worst == PIE_OK) {
+        worst = s;
+        msg = g_err;
+      }
+      continue;
+    }
+    if (s != PIE_OK) return s;
+  }
+  if (worst != PIE_OK) set_error(msg);
+  return worst;
+}
+
+pie_status pie_problem_quadrature(const pie_problem* h, double* pts, double* wts) {
+  if (!h) {
+    set_error("pie_problem_quadrature: NULL problem");
+    return PIE_ERR_PARAM;
+  }
+  const Problem& pr = h->p;
+  const Mesh& m = pr.mesh;
+  const std::vector<double>& r = pr.rule7_host;
+  for (int64_t t = 0; t < m.nt; ++t) {
+    const double* v0 = &m.xyz[3 * size_t(m.tri[3 * t])];
+    const double* v1 = &m.xyz[3 * size_t(m.tri[3 * t + 1])];
+    const double* v2 = &m.xyz[3 * size_t(m.tri[3 * t + 2])];
+    for (int q = 0; q < 7; ++q) {
+      if (pts)
+        for (int d = 0; d < 3; ++d)
+          pts[(t * 7 + q) * 3 + d] = r[4 * q] * v0[d] + r[4 * q + 1] * v1[d] + r[4 * q + 2] * v2[d];
+      if (wts) wts[t * 7 + q] = r[4 * q + 3] * m.area[t];
+    }
+  }
+  return PIE_OK;
+}
+
+pie_status pie_rhs_potentials(pie_problem* h, const void* A_q, const void* Phi_q, void* b, int dtype, void* stream) {
+  if (!h || !A_q || !Phi_q || !b) {
+    set_error("pie_rhs_potentials: NULL argument");
+    return PIE_ERR_PARAM;
+  }
+  if (dtype != (h->p.io_f32() ? PIE_C64 : PIE_C128)) {
+    set_error("pie_rhs_potentials: dtype does not match the problem precision");
+    return PIE_ERR_PARAM;
+  }
+  return rhs_potentials(h->p, A_q, Phi_q, b, static_cast<cudaStream_t>(stream));
 }
 
 static bool c128_problem(pie_problem* h, const char* who) {

@@ -985,6 +985,59 @@ pie_status rhs_planewave(Problem& pr, const double* khat, const double* pol, dou
   return cuda_check(cudaGetLastError(), "rhs launch");
 }
 
+// Right-hand side for potentials given at the 7 quadrature points of every
+// triangle (Eqs. (1)-(2)): U = -int (r - c_t).A, V = -int A, T1 = 0,
+// T2 = -i w eps0 int Phi, tested by k_assemble into b_J = -<f_m, A>,
+// b_sigma = -i w eps0 <p_t, Phi>.  Aq [T][7][3], Pq [T][7] in mesh order.
+template <typename Rio>
+__global__ void k_rhs_q(int64_t T, const int64_t* __restrict__ perm, const double* __restrict__ vert,
+                        const double* __restrict__ cent, const double* __restrict__ area, const cd* __restrict__ Aq,
+                        const cd* __restrict__ Pq, double weps, const double* __restrict__ rule,
+                        C2<Rio>* __restrict__ pot) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const int64_t m = perm[t];
+  const double* v = vert + 9 * t;
+  double Ur = 0, Ui = 0, Vr[3] = {0, 0, 0}, Vi[3] = {0, 0, 0}, Pr = 0, Pim = 0;
+  for (int q = 0; q < 7; ++q) {
+    const double b0 = rule[4 * q], b1 = rule[4 * q + 1], b2 = rule[4 * q + 2], wq = rule[4 * q + 3] * area[t];
+    const cd* A = Aq + (m * 7 + q) * 3;
+    const cd P = Pq[m * 7 + q];
+    for (int d = 0; d < 3; ++d) {
+      const double u = b0 * v[d] + b1 * v[3 + d] + b2 * v[6 + d] - cent[3 * t + d];
+      Ur += wq * u * A[d].x;
+      Ui += wq * u * A[d].y;
+      Vr[d] += wq * A[d].x;
+      Vi[d] += wq * A[d].y;
+    }
+    Pr += wq * P.x;
+    Pim += wq * P.y;
+  }
+  C2<Rio>* o = pot + 6 * t;
+  o[0] = mk<Rio>(Rio(-Ur), Rio(-Ui));
+  for (int d = 0; d < 3; ++d) o[1 + d] = mk<Rio>(Rio(-Vr[d]), Rio(-Vi[d]));
+  o[4] = mk<Rio>(0, 0);
+  o[5] = mk<Rio>(Rio(weps * Pim), Rio(-weps * Pr));
+}
+
+pie_status rhs_potentials(Problem& pr, const void* Aq, const void* Pq, void* b, cudaStream_t st) {
+  const double weps = pr.w * eps0();
+  const cd* A = static_cast<const cd*>(Aq);
+  const cd* P = static_cast<const cd*>(Pq);
+  if (pr.io_f32()) {
+    k_rhs_q<float><<<nblk(pr.T, 128), 128, 0, st>>>(pr.T, pr.perm, pr.vert, pr.cent, pr.area, A, P, weps, pr.rule7,
+                                                    static_cast<cf*>(pr.pot));
+    k_assemble<float><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                       pr.inv_perm, static_cast<cf*>(pr.pot), static_cast<cf*>(b));
+  } else {
+    k_rhs_q<double><<<nblk(pr.T, 128), 128, 0, st>>>(pr.T, pr.perm, pr.vert, pr.cent, pr.area, A, P, weps, pr.rule7,
+                                                     static_cast<cd*>(pr.pot));
+    k_assemble<double><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                        pr.inv_perm, static_cast<cd*>(pr.pot), static_cast<cd*>(b));
+  }
+  return cuda_check(cudaGetLastError(), "rhs launch");
+}
+
 // ---------------------------------------------------------------- far field
 
 // One block per direction: sum over triangles and quadrature points of

@@ -74,6 +74,7 @@ struct Problem {
   double* khat = nullptr;        // [P*3]
   double* wgt = nullptr;         // [P]
   double* rule7 = nullptr;       // [7][4] barycentric (3) + weight, 7-point rule
+  std::vector<double> rule7_host;  // the same rule on the host
   double* rule64 = nullptr;      // [64][4] collapsed Gauss 8 x 8
 
   // operator tables
@@ -127,6 +128,7 @@ pie_status apply_near_one(Problem& pr, const void* x, void* y, cudaStream_t st);
 pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, void* pot, cudaStream_t st);
 pie_status rhs_planewave(Problem& pr, const double* khat, const double* pol, double E0, void* b,
                          cudaStream_t st);
+pie_status rhs_potentials(Problem& pr, const void* Aq, const void* Pq, void* b, cudaStream_t st);
 pie_status farfield(Problem& pr, const void* x, const double* rhat, int64_t ndir, void* E,
                     cudaStream_t st);
 pie_status apply_t_one(Problem& pr, const void* x, void* y, bool conj, cudaStream_t st);

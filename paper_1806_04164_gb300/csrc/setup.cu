@@ -651,6 +651,7 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   pr.edge_tt = upload(pr, edge_tt, st, s);
   pr.edge_k = upload(pr, edge_k, st, s);
   pr.vert = upload(pr, vert, st, s);
+  pr.rule7_host = r7;
   pr.cent = upload(pr, cent, st, s);
   pr.h2 = upload(pr, h2, st, s);
   pr.area = upload(pr, area, st, s);

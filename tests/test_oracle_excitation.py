@@ -31,3 +31,32 @@ def test_fields_gauge_helmholtz():
     lap = sum((potentials(r + h * e, k, khat, pol)[1] - 2 * Phi + potentials(r - h * e, k, khat, pol)[1]) / h ** 2
               for e in np.eye(3))
     assert abs(lap + k * k * Phi) < 1e-5
+
+
+def test_rhs_from_potentials_closed_forms():
+    """Constant and linear potentials, whose testing integrals the 7-point
+    rule computes exactly: b_sigma = -i w eps0 A_t (phi0 + g.c_t) and
+    b_J[m] = -a0 . int f_m = -a0 . (l_m / 2) [(c+ - p+) - (c- - p-)]."""
+    import pie_inputs as pi
+    from oracle.excitation import quadrature_points, rhs_from_potentials
+    from oracle.mesh import build_topology
+    xyz, tri = pi.icosphere(2)
+    top = build_topology(xyz, tri)
+    k0 = 0.3
+    w = C.omega_of_k(k0)
+    P, W = quadrature_points(top)
+    assert np.allclose(W.sum(axis=1), top.area, rtol=1e-14, atol=0)
+    a0 = np.array([0.2 - 0.1j, -0.7 + 0.3j, 0.4 + 0.0j])
+    phi0, g = 1.3 - 0.2j, np.array([0.5, -0.25, 2.0])
+    A = np.broadcast_to(a0, P.shape)
+    Phi = phi0 + P @ g
+    b = rhs_from_potentials(top, k0, A, Phi)
+    want_s = -1j * w * C.EPS0 * top.area * (phi0 + top.centroid @ g)
+    assert np.allclose(b[top.E:], want_s, rtol=1e-13, atol=0)
+    want_J = np.zeros(top.E, np.complex128)
+    for n in range(top.E):
+        tp, tm = top.edge_tri[n]
+        pp, pm = top.xyz[top.edge_free[n, 0]], top.xyz[top.edge_free[n, 1]]
+        fint = 0.5 * top.edge_len[n] * ((top.centroid[tp] - pp) - (top.centroid[tm] - pm))
+        want_J[n] = -a0 @ fint
+    assert np.allclose(b[:top.E], want_J, rtol=1e-12, atol=1e-15 * np.abs(want_J).max())
