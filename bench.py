@@ -525,6 +525,7 @@ def gmres_run(pr, tol, k0, barrier, max_over_ranks):
     sm = rayleigh_eplane(k0, 1.0, -rh[:, 2])
     mask = sm > 1e-2 * sm.max()
     return {"tol": tol, "iterations": st["iterations"], "seconds": max_over_ranks(st["seconds"]),
+            "product_seconds": st["product_seconds"], "reorthogonalizations": st["reorthogonalizations"],
             "rel_residual": st["rel_residual"], "converged": st["converged"], "restart": 300,
             "rcs_max_db_err_vs_rayleigh": float(np.max(np.abs(10 * np.log10(s[mask] / sm[mask])))),
             "rcs_db": [float(v) for v in 10 * np.log10(s[::30])]}

@@ -100,6 +100,8 @@ typedef struct {
   int32_t iterations;         /* Arnoldi steps taken */
   double rel_residual;        /* ||b - Z x|| / ||b||, recomputed in FP64 */
   double seconds;             /* wall time of the solve */
+  int32_t reorthogonalizations; /* Arnoldi steps that took a second Gram-Schmidt pass */
+  double product_seconds;     /* part of `seconds` in operator products (CUDA events) */
 } pie_solve_stats;
 
 /* Message of the last failed call on this thread ("" if none). */

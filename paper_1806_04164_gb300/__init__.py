@@ -51,7 +51,8 @@ class Tuning(ctypes.Structure):
 
 
 class SolveStats(ctypes.Structure):
-    _fields_ = [("iterations", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+    _fields_ = [("iterations", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("reorthogonalizations", ctypes.c_int32), ("product_seconds", ctypes.c_double)]
 
 
 _lib = None
@@ -310,7 +311,8 @@ class Problem:
         if code not in (0, 8):
             _check(code)
         return x, dict(iterations=st.iterations, rel_residual=st.rel_residual, seconds=st.seconds,
-                       converged=code == 0)
+                       converged=code == 0, reorthogonalizations=st.reorthogonalizations,
+                       product_seconds=st.product_seconds)
 
     def rhs_potential(self, khat, pol, E0=1.0, stream=None):
         """b_t = <p_t, Phi^inc> for the plane wave (right-hand side of Eq. (3))."""
@@ -414,7 +416,8 @@ class Problem:
         if code not in (0, 8):
             _check(code)
         stats = [dict(iterations=s.iterations, rel_residual=s.rel_residual, seconds=s.seconds,
-                      converged=s.rel_residual <= tol) for s in st[:nrhs]]
+                      converged=s.rel_residual <= tol, reorthogonalizations=s.reorthogonalizations,
+                      product_seconds=s.product_seconds) for s in st[:nrhs]]
         return (x, stats[0]) if b.dim() == 1 else (x, stats)
 
     @property

@@ -119,68 +119,109 @@ __global__ void k_axs(int64_t N, double alpha, const C2<B>* __restrict__ x, C2<B
 }
 
 // partial[v][tile] = sum over the tile's entries of conj(V[v][n]) w[n]
-// (accumulated in the basis type inside a tile, then in double).  Pass 1 of a
-// fixed-order reduction; grid = (tiles, vectors), all vectors in parallel.
-constexpr int kTile = 4096;
+// (accumulated in the basis type per thread, then in double).  Pass 1 of a
+// fixed-order reduction.  A block takes one tile of w into registers and
+// runs it against a chunk of kVecChunk vectors, so w is read once per chunk
+// and every thread has kVecChunk x kPerThread loads in flight; grid = (tiles,
+// vector chunks).
+constexpr int kPerThread = 8;
+constexpr int kTile = kRedThreads * kPerThread;
+constexpr int kVecChunk = 8;
 template <typename B>
 __global__ void __launch_bounds__(kRedThreads) k_mdot(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv,
                                                       const C2<B>* __restrict__ w, cd* __restrict__ partial) {
-  __shared__ double sr[kRedThreads / 32], si[kRedThreads / 32];
-  const int v = blockIdx.y;
-  const int64_t n0 = int64_t(blockIdx.x) * kTile, n1 = min(N, n0 + kTile);
-  const C2<B>* vv = V + v * ldv;
-  B ar = 0, ai = 0;
-  for (int64_t n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-    C2<B> a = vv[n], b = w[n];
-    ar += a.x * b.x + a.y * b.y;
-    ai += a.x * b.y - a.y * b.x;
+  constexpr int NW = kRedThreads / 32;
+  __shared__ double sr[kVecChunk][NW], si[kVecChunk][NW];
+  const int v0 = blockIdx.y * kVecChunk, nvc = min(kVecChunk, nv - v0);
+  const int64_t n0 = int64_t(blockIdx.x) * kTile + threadIdx.x;
+  C2<B> wr[kPerThread];
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int64_t n = n0 + int64_t(k) * kRedThreads;
+    wr[k] = n < N ? w[n] : mk<B>(0, 0);
   }
-  double dr = warp_sum(double(ar)), di = warp_sum(double(ai));
-  if ((threadIdx.x & 31) == 0) {
-    sr[threadIdx.x >> 5] = dr;
-    si[threadIdx.x >> 5] = di;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < kVecChunk; ++c) {
+    if (c >= nvc) break;
+    const C2<B>* vv = V + int64_t(v0 + c) * ldv;
+    B ar = 0, ai = 0;
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+      const int64_t n = n0 + int64_t(k) * kRedThreads;
+      if (n < N) {
+        const C2<B> a = vv[n], b = wr[k];
+        ar += a.x * b.x + a.y * b.y;
+        ai += a.x * b.y - a.y * b.x;
+      }
+    }
+    const double dr = warp_sum(double(ar)), di = warp_sum(double(ai));
+    if (lane == 0) {
+      sr[c][warp] = dr;
+      si[c][warp] = di;
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < nvc) {
     double tr = 0, ti = 0;
-    for (int k = 0; k < kRedThreads / 32; ++k) {
-      tr += sr[k];
-      ti += si[k];
+    for (int k = 0; k < NW; ++k) {
+      tr += sr[threadIdx.x][k];
+      ti += si[threadIdx.x][k];
     }
-    partial[(int64_t)v * gridDim.x + blockIdx.x] = mk<double>(tr, ti);
+    partial[int64_t(v0 + threadIdx.x) * gridDim.x + blockIdx.x] = mk<double>(tr, ti);
   }
 }
 
-// Pass 2: out[v] = sum over tiles of partial[v][.], in tile order.
+// Pass 2: out[v] = sum over tiles of partial[v][.], one warp per vector,
+// lanes over tiles in a fixed order, then a fixed shuffle tree.
 __global__ void k_mdot_finish(int nv, int nblk, const cd* __restrict__ partial, cd* __restrict__ out) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (v >= nv) return;
   double r = 0, i = 0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     r += partial[(int64_t)v * nblk + b].x;
     i += partial[(int64_t)v * nblk + b].y;
   }
-  out[v] = mk<double>(r, i);
+  r = warp_sum(r);
+  i = warp_sum(i);
+  if (lane == 0) out[v] = mk<double>(r, i);
 }
 
-// w -= sum_v h[v] V[v], in the basis type; h staged in shared memory.
+// w -= sum_v h[v] V[v] (in the basis type, h staged in shared memory),
+// followed by the squared norm of the updated w: per-block
+// partial sums (fixed order) in partial[blockIdx.x], finished by
+// k_mdot_finish.  Block size kRedThreads.
 template <typename B>
-__global__ void k_mupdate(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv, const cd* __restrict__ h,
-                          C2<B>* __restrict__ w) {
+__global__ void __launch_bounds__(kRedThreads) k_mupdate_norm(int64_t N, int nv, const C2<B>* __restrict__ V,
+                                                              int64_t ldv, const cd* __restrict__ h,
+                                                              C2<B>* __restrict__ w, cd* __restrict__ partial) {
   extern __shared__ unsigned char hraw[];
   C2<B>* hs = reinterpret_cast<C2<B>*>(hraw);
+  __shared__ double sn[kRedThreads / 32];
   for (int v = threadIdx.x; v < nv; v += blockDim.x) hs[v] = mk<B>(B(h[v].x), B(h[v].y));
   __syncthreads();
-  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  B r = 0, i = 0;
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double nrm = 0;
+  if (n < N) {
+    B r = 0, i = 0;
 #pragma unroll 4
-  for (int v = 0; v < nv; ++v) {
-    C2<B> a = V[v * ldv + n], c = hs[v];
-    r += c.x * a.x - c.y * a.y;
-    i += c.x * a.y + c.y * a.x;
+    for (int v = 0; v < nv; ++v) {
+      C2<B> a = V[v * ldv + n], c = hs[v];
+      r += c.x * a.x - c.y * a.y;
+      i += c.x * a.y + c.y * a.x;
+    }
+    const C2<B> o = mk<B>(w[n].x - r, w[n].y - i);
+    w[n] = o;
+    nrm = double(o.x) * double(o.x) + double(o.y) * double(o.y);
   }
-  w[n] = mk<B>(w[n].x - r, w[n].y - i);
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) sn[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < kRedThreads / 32; ++k) t += sn[k];
+    partial[blockIdx.x] = mk<double>(t, 0.0);
+  }
 }
 
 // x += d (sum_v y[v] V[v]) in complex double (the solution stays FP64).
@@ -235,21 +276,74 @@ struct Ctx {
   cd* wd;           // operator output (double)
   cd* partial;      // reduction partials
   cd* hdev;         // small device vector
+  int hcap = 0;     // its length (the last entry holds norms)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last operator product
+  bool pending = false;                      // ev0 / ev1 hold a product not yet counted
+  double op_ms = 0;                          // time in operator products
+  int reorth = 0;                            // second Gram-Schmidt passes
 };
+
+// Adds the last product's time (its events have completed: every product is
+// followed by a synchronising reduction before the next one).
+static void op_time_flush(Ctx& c) {
+  if (!c.pending || !c.ev0) return;
+  float ms = 0;
+  if (cudaEventElapsedTime(&ms, c.ev0, c.ev1) == cudaSuccess)
+    c.op_ms += ms;
+  else
+    cudaGetLastError();
+  c.pending = false;
+}
 
 // out = Z in, or out = S in for the single-layer operator of Eq. (3).
 static pie_status op_apply(Ctx& c, const cd* in, cd* out) {
-  return c.op == 0 ? apply_one(c.pr, in, out, c.st) : single_layer_one(c.pr, in, out, c.st);
+  op_time_flush(c);
+  if (c.ev0) cudaEventRecord(c.ev0, c.st);
+  pie_status s = c.op == 0 ? apply_one(c.pr, in, out, c.st) : single_layer_one(c.pr, in, out, c.st);
+  if (c.ev1) {
+    cudaEventRecord(c.ev1, c.st);
+    c.pending = true;
+  }
+  return s;
 }
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() {
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      a = b = nullptr;  // timing of the products is then left out
+    }
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
 
 // conj(a) . b over N entries, deterministic; result on the host.
 template <typename B>
 static pie_status dotc(Ctx& c, int nv, const C2<B>* V, const C2<B>* w, zc* out_host) {
   const unsigned tiles = unsigned((c.N + kTile - 1) / kTile);
-  k_mdot<B><<<dim3(tiles, unsigned(nv)), kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w, c.partial);
-  k_mdot_finish<<<nb_(nv, 128), 128, 0, c.st>>>(nv, int(tiles), c.partial, c.hdev);
+  k_mdot<B><<<dim3(tiles, unsigned((nv + kVecChunk - 1) / kVecChunk)), kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w,
+                                                                                              c.partial);
+  k_mdot_finish<<<nb_(int64_t(nv) * 32, 128), 128, 0, c.st>>>(nv, int(tiles), c.partial, c.hdev);
   pie_status s = cuda_check(cudaMemcpyAsync(out_host, c.hdev, sizeof(cd) * nv, cudaMemcpyDeviceToHost, c.st), "dot");
   if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "dot sync");
+  return s;
+}
+
+// w -= sum_{v<nv} hdev[v] V[v]; returns ||w|| (host) after the update.
+template <typename B>
+static pie_status update_norm(Ctx& c, int nv, const C2<B>* V, C2<B>* w, double* norm) {
+  const unsigned blocks = nb_(c.N, kRedThreads);
+  k_mupdate_norm<B><<<blocks, kRedThreads, sizeof(C2<B>) * nv, c.st>>>(c.N, nv, V, c.N, c.hdev, w, c.partial);
+  k_mdot_finish<<<1, 32, 0, c.st>>>(1, int(blocks), c.partial, c.hdev + c.hcap - 1);
+  cd out;
+  pie_status s = cuda_check(cudaMemcpyAsync(&out, c.hdev + c.hcap - 1, sizeof(cd), cudaMemcpyDeviceToHost, c.st),
+                            "norm");
+  if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "norm sync");
+  *norm = std::sqrt(out.x);
   return s;
 }
 
@@ -272,7 +366,7 @@ struct Cycle {
 // residual falls below stop_abs.  On return y (host) holds the coefficients
 // and j the number of steps.
 template <typename B>
-static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, C2<B>* w, Cycle& cy, double beta, double stop_abs, int max_steps,
+static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, Cycle& cy, double beta, double stop_abs, int max_steps,
                                 int& j_out, std::vector<zc>& y, bool& breakdown, int& steps_done) {
   const int64_t N = c.N;
   const int m = cy.m;
@@ -282,27 +376,25 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, C2<B>* w, Cycle& cy, double be
   cy.g[0] = beta;
   int j = 0;
   breakdown = false;
-  zc tmp[1];
   for (; j < m && j < max_steps; ++j) {
     const C2<B>* vj = V + size_t(j) * N;
-    // w = D Z D v_j
+    // the new vector is built in its own basis slot: w = D Z D v_j
+    C2<B>* w = V + size_t(j + 1) * N;
     k_scale<B, double><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, vj, c.u);
     if ((s = op_apply(c, c.u, c.wd)) != PIE_OK) return s;
     k_scale<double, B><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, c.wd, w);
     // classical Gram-Schmidt; a second pass only when the first one cancelled
-    // most of w (Daniel-Gragg-Kaufman-Stewart criterion)
-    if ((s = dotc<B>(c, 1, w, w, tmp)) != PIE_OK) return s;
-    const double wn0 = std::sqrt(tmp[0].real());
-    if ((s = dotc<B>(c, j + 1, V, w, cy.h.data())) != PIE_OK) return s;
-    k_mupdate<B><<<nb_(N, 256), 256, sizeof(C2<B>) * (j + 1), c.st>>>(N, j + 1, V, N, c.hdev, w);
-    if ((s = dotc<B>(c, 1, w, w, tmp)) != PIE_OK) return s;
-    double hn = std::sqrt(tmp[0].real());
+    // most of w (Daniel-Gragg-Kaufman-Stewart criterion).  One reduction
+    // gives (v_i, w) for i <= j and (w, w); the update returns the new norm.
+    if ((s = dotc<B>(c, j + 2, V, w, cy.h.data())) != PIE_OK) return s;
+    const double wn0 = std::sqrt(cy.h[j + 1].real());
+    double hn = 0;
+    if ((s = update_norm<B>(c, j + 1, V, w, &hn)) != PIE_OK) return s;
     if (hn < 0.7 * wn0) {
+      ++c.reorth;
       if ((s = dotc<B>(c, j + 1, V, w, cy.h2.data())) != PIE_OK) return s;
-      k_mupdate<B><<<nb_(N, 256), 256, sizeof(C2<B>) * (j + 1), c.st>>>(N, j + 1, V, N, c.hdev, w);
+      if ((s = update_norm<B>(c, j + 1, V, w, &hn)) != PIE_OK) return s;
       for (int i = 0; i <= j; ++i) cy.h[i] += cy.h2[i];
-      if ((s = dotc<B>(c, 1, w, w, tmp)) != PIE_OK) return s;
-      hn = std::sqrt(tmp[0].real());
     }
     for (int i = 0; i <= j; ++i)
       if (!std::isfinite(cy.h[i].real()) || !std::isfinite(cy.h[i].imag()) || !std::isfinite(hn)) {
@@ -329,7 +421,7 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, C2<B>* w, Cycle& cy, double be
       ++j;
       break;
     }
-    k_axs<B><<<nb_(N, 256), 256, 0, c.st>>>(N, 1.0 / hn, w, V + size_t(j + 1) * N);
+    k_axs<B><<<nb_(N, 256), 256, 0, c.st>>>(N, 1.0 / hn, w, w);
     if (std::abs(cy.g[j + 1]) <= stop_abs) {
       ++j;
       break;
@@ -360,14 +452,19 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
   Work wk;
   double* d = wk.get<double>(N, s);
   C2<B>* V = wk.get<C2<B>>(size_t(N) * (m + 1), s);
-  C2<B>* w = wk.get<C2<B>>(N, s);
   cd* u = wk.get<cd>(N, s);
   cd* wd = wk.get<cd>(N, s);
   cd* r = wk.get<cd>(N, s);
-  cd* partial = wk.get<cd>(size_t((N + kTile - 1) / kTile) * (m + 2), s);
-  cd* hdev = wk.get<cd>(m + 1, s);
+  cd* partial = wk.get<cd>(std::max(size_t((N + kTile - 1) / kTile) * (m + 2), size_t(nb_(N, kRedThreads))), s);
+  cd* hdev = wk.get<cd>(m + 3, s);
   if (s != PIE_OK) return s;
+  EventPair evp;
   Ctx c{pr, st, op, N, d, u, wd, partial, hdev};
+  c.hcap = m + 3;
+  if (evp.a && evp.b) {
+    c.ev0 = evp.a;
+    c.ev1 = evp.b;
+  }
   const cd* b = static_cast<const cd*>(bv);
   cd* x = static_cast<cd*>(xv);
   const double w2e = pr.w * pr.w * eps0();
@@ -416,7 +513,7 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
     int j = 0;
     bool breakdown = false;
     const double dbn = beta / rel;  // scale of ||D b|| for the cycle's stopping estimate
-    if ((s = arnoldi_cycle<B>(c, V, w, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, breakdown, it)) != PIE_OK)
+    if ((s = arnoldi_cycle<B>(c, V, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, breakdown, it)) != PIE_OK)
       return s;
     // x += D (sum_j y_j V_j), in complex double
     if ((s = to_dev(c, y, j)) != PIE_OK) return s;
@@ -442,10 +539,13 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
       set_error("pie_solve: tolerance not reached in maxit iterations");
   }
   if ((s = cuda_check(cudaStreamSynchronize(st), "gmres sync")) != PIE_OK) return s;
+  op_time_flush(c);
   if (stats) {
     stats->iterations = it;
     stats->rel_residual = rel;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->reorthogonalizations = c.reorth;
+    stats->product_seconds = c.op_ms * 1e-3;
   }
   return result;
 }
