@@ -347,16 +347,36 @@ __device__ __forceinline__ void apply_split_block(const C2<Rf>* a, const Rf* KE,
 template <int NT, typename Rf>
 __host__ __device__ constexpr size_t fft_smem_bytes(bool interp) {
   constexpr int NPHI = 2 * NT, P = NT * NPHI;
-  return sizeof(C2<Rf>) * (size_t(kFftBatch) * kComp * NPHI * (NT + 1) + size_t(kFftBatch) * kComp * NT * (NPHI + 1) +
-                           (interp ? size_t(kComp) * P : 0)) +
+  return sizeof(C2<Rf>) * (size_t(kFftBatch) * kComp * NPHI * (NT + 1) + (interp ? size_t(kComp) * P : 0)) +
          sizeof(Rf) * 2 * NPHI * (NT / 2) * (NT / 2);
 }
 
-// a3 (factorised): one block per parent box, kFftBatch children at a time,
-// one thread per (child, component, theta row) for the DFTs and per (child,
+// One K_m block in place on a spectrum column (NT theta rows, stride 1):
+// K_8 = 0, the others through their mirror-split halves.
+template <int NT, typename Rf>
+__device__ __forceinline__ void filter_column(C2<Rf>* col, int m, const Rf* KE, const Rf* KO) {
+  constexpr int NPHI = 2 * NT, H = NT / 2;
+  if (m == NPHI / 2) {
+#pragma unroll
+    for (int i = 0; i < NT; ++i) col[i] = mk<Rf>(0, 0);
+    return;
+  }
+  C2<Rf> a[NT];
+#pragma unroll
+  for (int i = 0; i < NT; ++i) a[i] = col[i];
+  apply_split_block<NT, 1>(a, KE + m * H * H, KO + m * H * H, col);
+}
+
+// a3 (factorised): one block per parent box, kFftBatch children at a time.
+// Per (child, component) one shared-memory region of NPHI x (NT+1) complex
+// holds, in turn, the row spectra [m][i], the filtered spectra (the K_m
+// blocks act in place on each column m), and the shifted child pattern, row
+// i written over the row's own spectra ([j][i]) before it is added to the
+// parent's.  Threads:
+// one per (child, component, theta row) for the DFTs, one per (child,
 // component, azimuthal frequency) for the K_m blocks.
 template <int NT, typename Rf>
-__global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
+__global__ void __launch_bounds__(kFftBatch * kComp * NT, 3) k_interp_fft(
     const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Sc,
     const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Sp, int64_t sSc = 0,
     int64_t sSp = 0) {
@@ -364,80 +384,66 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_interp_fft(
   Sc += blockIdx.y * sSc;
   Sp += blockIdx.y * sSp;
   constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch, H = NT / 2;
-  // rows padded by one element (AP, BP) so that lanes striding over rows hit
-  // distinct shared-memory banks
-  constexpr int AP = NT + 1, BP = NPHI + 1;
+  // AP: column stride of the spectra (padded by one so that lanes striding
+  // over columns hit distinct banks)
+  constexpr int AP = NT + 1, REG = NPHI * AP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);  // spectra [slot][c][m][i (AP)], then results [slot][c][i][j (BP)]
-  C2<Rf>* B = A + NB * kComp * NPHI * AP;             // filtered spectra [slot][c][i][m (BP)]
-  C2<Rf>* acc = B + NB * kComp * NT * BP;             // parent pattern [c][p]
+  C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);  // [slot][c] regions of REG complex
+  C2<Rf>* acc = A + NB * kComp * REG;                 // parent pattern [c][p]
   Rf* KE = reinterpret_cast<Rf*>(acc + kComp * P);    // mirror-split K_m blocks
   Rf* KO = KE + NPHI * H * H;
   const int tid = threadIdx.x, nth = blockDim.x;
   load_split_blocks<NT, false>(Kf, KE, KO, tid, nth);
   for (int i = tid; i < kComp * P; i += nth) acc[i] = mk<Rf>(0, 0);
   const int b = blockIdx.x, c0 = child_start[b], c1 = child_start[b + 1];
+  const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
   for (int base = c0; base < c1; base += NB) {
     const int nb = min(NB, c1 - base);
+    C2<Rf>* R = A + (slot * kComp + c) * REG;
     __syncthreads();
-    {  // forward DFT of every row
-      const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
-      if (slot < nb) {
-        C2<Rf> x[NPHI], X[NPHI];
-        const C2<Rf>* src = Sc + ((int64_t)(base + slot) * kComp + c) * P + i * NPHI;
+    if (slot < nb) {  // forward DFT of every row
+      C2<Rf> x[NPHI], X[NPHI];
+      const C2<Rf>* src = Sc + ((int64_t)(base + slot) * kComp + c) * P + i * NPHI;
 #pragma unroll
-        for (int j = 0; j < NPHI; ++j) x[j] = src[j];
-        fft16<false>(x, X);
+      for (int j = 0; j < NPHI; ++j) x[j] = src[j];
+      fft16<false>(x, X);
 #pragma unroll
-        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * AP + i] = X[m];
-      }
+      for (int m = 0; m < NPHI; ++m) R[m * AP + i] = X[m];
     }
     __syncthreads();
-    for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // K_m blocks (K_8 = 0)
-      const int sc = it / NPHI, m = it % NPHI;
-      C2<Rf>* out = B + sc * NT * BP + m;
-      if (m == NPHI / 2) {
+    for (int it = tid; it < nb * kComp * NPHI; it += nth)  // K_m blocks, in place
+      filter_column<NT>(A + (it / NPHI) * REG + (it % NPHI) * AP, it % NPHI, KE, KO);
+    __syncthreads();
+    if (slot < nb) {  // inverse DFT, phase shift to the parent centre, in the row's own column
+      C2<Rf> x[NPHI], X[NPHI];
 #pragma unroll
-        for (int i = 0; i < NT; ++i) out[i * BP] = mk<Rf>(0, 0);
-      } else {
-        apply_split_block<NT, BP>(A + (sc * NPHI + m) * AP, KE + m * H * H, KO + m * H * H, out);
-      }
+      for (int m = 0; m < NPHI; ++m) x[m] = R[m * AP + i];
+      fft16<true>(x, X);
+      const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
+#pragma unroll
+      for (int j = 0; j < NPHI; ++j) R[j * AP + i] = cmul(ph[j], X[j]);
     }
     __syncthreads();
-    {  // inverse DFT, phase shift to the parent centre
-      const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
-      if (slot < nb) {
-        C2<Rf> x[NPHI], X[NPHI];
-        const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * BP;
-#pragma unroll
-        for (int m = 0; m < NPHI; ++m) x[m] = src[m];
-        fft16<true>(x, X);
-        const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
-        C2<Rf>* dst = A + ((slot * kComp + c) * NT + i) * BP;
-#pragma unroll
-        for (int j = 0; j < NPHI; ++j) dst[j] = cmul(ph[j], X[j]);
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < kComp * P; i += nth) {
-      const int row = i / NPHI, j = i % NPHI;  // row = c * NT + theta row
-      C2<Rf> v = acc[i];
-      for (int slot = 0; slot < nb; ++slot) {
-        C2<Rf> u = A[(slot * kComp * NT + row) * BP + j];
+    for (int k = tid; k < kComp * P; k += nth) {
+      const int cc = k / P, row = (k / NPHI) % NT, j = k % NPHI;
+      C2<Rf> v = acc[k];
+      for (int s = 0; s < nb; ++s) {
+        const C2<Rf> u = A[(s * kComp + cc) * REG + j * AP + row];
         v.x += u.x;
         v.y += u.y;
       }
-      acc[i] = v;
+      acc[k] = v;
     }
   }
   __syncthreads();
-  for (int i = tid; i < kComp * P; i += nth) Sp[(int64_t)b * kComp * P + i] = acc[i];
+  for (int k = tid; k < kComp * P; k += nth) Sp[(int64_t)b * kComp * P + k] = acc[k];
 }
 
 // a5 (factorised): one block per parent box; its children take
-// F^T (conj(phase_o) G_parent), added to their incoming patterns.
+// F^T (conj(phase_o) G_parent), added to their incoming patterns.  Same
+// shared-memory regions as k_interp_fft, without the parent accumulator.
 template <int NT, typename Rf>
-__global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
+__global__ void __launch_bounds__(kFftBatch * kComp * NT, 4) k_anterp_fft(
     const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Gp,
     const Rf* __restrict__ Kf, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Gc, int64_t sGp = 0,
     int64_t sGc = 0) {
@@ -445,60 +451,46 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT) k_anterp_fft(
   Gp += blockIdx.y * sGp;
   Gc += blockIdx.y * sGc;
   constexpr int NPHI = 2 * NT, P = NT * NPHI, NB = kFftBatch, H = NT / 2;
-  constexpr int AP = NT + 1, BP = NPHI + 1;  // padded rows (bank spreading)
+  constexpr int AP = NT + 1, REG = NPHI * AP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<Rf>* A = reinterpret_cast<C2<Rf>*>(smem_raw);
-  C2<Rf>* B = A + NB * kComp * NPHI * AP;
-  Rf* KE = reinterpret_cast<Rf*>(B + NB * kComp * NT * BP);
+  Rf* KE = reinterpret_cast<Rf*>(A + NB * kComp * REG);
   Rf* KO = KE + NPHI * H * H;
   const int tid = threadIdx.x, nth = blockDim.x;
   load_split_blocks<NT, true>(Kf, KE, KO, tid, nth);
   const int b = blockIdx.x, c0 = child_start[b], c1 = child_start[b + 1];
+  const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
   for (int base = c0; base < c1; base += NB) {
     const int nb = min(NB, c1 - base);
+    C2<Rf>* R = A + (slot * kComp + c) * REG;
     __syncthreads();
-    {
-      const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
-      if (slot < nb) {
-        C2<Rf> x[NPHI], X[NPHI];
-        const C2<Rf>* src = Gp + ((int64_t)b * kComp + c) * P + i * NPHI;
-        const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
+    if (slot < nb) {
+      C2<Rf> x[NPHI], X[NPHI];
+      const C2<Rf>* src = Gp + ((int64_t)b * kComp + c) * P + i * NPHI;
+      const C2<Rf>* ph = phase + oct_child[base + slot] * P + i * NPHI;
 #pragma unroll
-        for (int j = 0; j < NPHI; ++j) {
-          C2<Rf> g = src[j], w = ph[j];
-          x[j] = mk<Rf>(w.x * g.x + w.y * g.y, w.x * g.y - w.y * g.x);  // conj(w) g
-        }
-        fft16<false>(x, X);
-#pragma unroll
-        for (int m = 0; m < NPHI; ++m) A[((slot * kComp + c) * NPHI + m) * AP + i] = X[m];
+      for (int j = 0; j < NPHI; ++j) {
+        C2<Rf> g = src[j], w = ph[j];
+        x[j] = mk<Rf>(w.x * g.x + w.y * g.y, w.x * g.y - w.y * g.x);  // conj(w) g
       }
+      fft16<false>(x, X);
+#pragma unroll
+      for (int m = 0; m < NPHI; ++m) R[m * AP + i] = X[m];
     }
     __syncthreads();
-    for (int it = tid; it < nb * kComp * NPHI; it += nth) {  // transposed K_m blocks (K_8 = 0)
-      const int sc = it / NPHI, m = it % NPHI;
-      C2<Rf>* out = B + sc * NT * BP + m;
-      if (m == NPHI / 2) {
-#pragma unroll
-        for (int i = 0; i < NT; ++i) out[i * BP] = mk<Rf>(0, 0);
-      } else {
-        apply_split_block<NT, BP>(A + (sc * NPHI + m) * AP, KE + m * H * H, KO + m * H * H, out);
-      }
-    }
+    for (int it = tid; it < nb * kComp * NPHI; it += nth)  // transposed K_m blocks, in place
+      filter_column<NT>(A + (it / NPHI) * REG + (it % NPHI) * AP, it % NPHI, KE, KO);
     __syncthreads();
-    {
-      const int slot = tid / (kComp * NT), c = (tid / NT) % kComp, i = tid % NT;
-      if (slot < nb) {
-        C2<Rf> x[NPHI], X[NPHI];
-        const C2<Rf>* src = B + ((slot * kComp + c) * NT + i) * BP;
+    if (slot < nb) {
+      C2<Rf> x[NPHI], X[NPHI];
 #pragma unroll
-        for (int m = 0; m < NPHI; ++m) x[m] = src[m];
-        fft16<true>(x, X);
-        C2<Rf>* dst = Gc + ((int64_t)(base + slot) * kComp + c) * P + i * NPHI;
+      for (int m = 0; m < NPHI; ++m) x[m] = R[m * AP + i];
+      fft16<true>(x, X);
+      C2<Rf>* dst = Gc + ((int64_t)(base + slot) * kComp + c) * P + i * NPHI;
 #pragma unroll
-        for (int j = 0; j < NPHI; ++j) {
-          C2<Rf> g = dst[j];
-          dst[j] = mk<Rf>(g.x + X[j].x, g.y + X[j].y);
-        }
+      for (int j = 0; j < NPHI; ++j) {
+        C2<Rf> g = dst[j];
+        dst[j] = mk<Rf>(g.x + X[j].x, g.y + X[j].y);
       }
     }
   }
