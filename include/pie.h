@@ -331,13 +331,18 @@ pie_status pie_nearfield(pie_problem* pr, const void* x, const void* rho, const 
  *    that it takes a bounded share of every SM beside the far kernels;
  *    0 = one warp per test triangle.  0..32.
  *  rhs_chunk: right-hand sides per pass over the operator, 1..max_nrhs.
+ *  near_rhs_block: right-hand sides that one thread of the near kernel
+ *    carries (each pair's moments are read once for them): 1, 2, 4 or 8, or
+ *    0 to pick by the pass width (1 for one column, 2 for two or a complex
+ *    double near part, 4 up to four, else 8).
  * Defaults at pie_problem_create: overlap 1, near_ctas_per_sm 2, rhs_chunk
- * max_nrhs.  Per-stage profiling (pie_profile_begin) runs the stages in
- * order whatever overlap says. */
+ * max_nrhs, near_rhs_block 0.  Per-stage profiling (pie_profile_begin) runs
+ * the stages in order whatever overlap says. */
 typedef struct pie_tuning {
   int32_t overlap;
   int32_t near_ctas_per_sm;
   int32_t rhs_chunk;
+  int32_t near_rhs_block;
 } pie_tuning;
 
 pie_status pie_problem_get_tuning(const pie_problem* pr, pie_tuning* t);
@@ -347,11 +352,12 @@ pie_status pie_problem_set_tuning(pie_problem* pr, const pie_tuning* t);
 /* Autotuner: times products of nrhs right-hand sides (1..1024; library
  * scratch, contents irrelevant to the timing) under each candidate setting
  * -- overlap off, overlap with near_ctas_per_sm in {1, 2, 3, 4, 6, 8, 0},
- * rhs_chunk in the powers of two up to min(nrhs, max_nrhs) -- by CUDA events
- * on the stream, median of reps (1..100) after one warm-up each, keeps the
- * fastest, and returns it (best, host) with its milliseconds per
- * right-hand side (best_ms, host, may be NULL).  The search is greedy: the
- * overlap grid at the largest rhs_chunk first, then rhs_chunk.  Allocates
+ * rhs_chunk in the powers of two up to min(nrhs, max_nrhs), near_rhs_block
+ * in {1, 2, 4, 8} up to the chosen chunk -- by CUDA events on the stream,
+ * median of reps (1..100) after one warm-up each, keeps the fastest, and
+ * returns it (best, host) with its milliseconds per right-hand side
+ * (best_ms, host, may be NULL).  The search is greedy: the overlap grid at
+ * the largest rhs_chunk first, then rhs_chunk, then near_rhs_block.  Allocates
  * 2 x nrhs x N complex of scratch for its duration; synchronises the stream.
  * Errors: PIE_ERR_PARAM, PIE_ERR_OOM, PIE_ERR_CUDA. */
 pie_status pie_problem_autotune(pie_problem* pr, int nrhs, int reps, pie_tuning* best, double* best_ms,

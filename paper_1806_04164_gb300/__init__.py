@@ -44,10 +44,12 @@ class Info(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("overlap", ctypes.c_int32), ("near_ctas_per_sm", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32)]
+    _fields_ = [("overlap", ctypes.c_int32), ("near_ctas_per_sm", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
+                ("near_rhs_block", ctypes.c_int32)]
 
     def as_dict(self):
-        return dict(overlap=self.overlap, near_ctas_per_sm=self.near_ctas_per_sm, rhs_chunk=self.rhs_chunk)
+        return dict(overlap=self.overlap, near_ctas_per_sm=self.near_ctas_per_sm, rhs_chunk=self.rhs_chunk,
+                    near_rhs_block=self.near_rhs_block)
 
 
 class SolveStats(ctypes.Structure):

@@ -755,13 +755,15 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
         pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
         static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot2, nrhs, sT, sT);
   };
+  int rb = pr.tune.near_rhs_block;
+  if (rb == 0) rb = nrhs == 1 ? 1 : (nrhs == 2 || sizeof(Rm) == 8) ? 2 : nrhs <= 4 ? 4 : 8;
   if (!with_near)
     pot2 = nullptr;
-  else if (nrhs == 1)
+  else if (rb == 1)
     near_launch(std::integral_constant<int, 1>());
-  else if (nrhs == 2 || sizeof(Rm) == 8)
+  else if (rb == 2)
     near_launch(std::integral_constant<int, 2>());
-  else if (nrhs <= 4)
+  else if (rb == 4)
     near_launch(std::integral_constant<int, 4>());
   else
     near_launch(std::integral_constant<int, 8>());

@@ -102,7 +102,7 @@ struct Problem {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int nsm = 0;                   // SMs of the device
-  pie_tuning tune{1, 2, 1};
+  pie_tuning tune{1, 2, 1, 0};
   // parts of the product that run (pie_apply_levels): translations at the
   // levels whose bit is set, and the near part
   uint32_t far_mask = 0xffffffffu;

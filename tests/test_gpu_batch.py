@@ -25,16 +25,18 @@ def columns(n, nrhs, seed):
     return torch.from_numpy(np.stack([pi.complex_normal(n, seed + j) for j in range(nrhs)])).cuda()
 
 
-SETTINGS = [dict(overlap=0, near_ctas_per_sm=0, rhs_chunk=4), dict(overlap=1, near_ctas_per_sm=1, rhs_chunk=4),
-            dict(overlap=1, near_ctas_per_sm=3, rhs_chunk=2), dict(overlap=1, near_ctas_per_sm=0, rhs_chunk=1),
-            dict(overlap=0, near_ctas_per_sm=5, rhs_chunk=3)]
+SETTINGS = [dict(overlap=0, near_ctas_per_sm=0, rhs_chunk=4, near_rhs_block=0),
+            dict(overlap=1, near_ctas_per_sm=1, rhs_chunk=4, near_rhs_block=1),
+            dict(overlap=1, near_ctas_per_sm=3, rhs_chunk=2, near_rhs_block=8),
+            dict(overlap=1, near_ctas_per_sm=0, rhs_chunk=1, near_rhs_block=2),
+            dict(overlap=0, near_ctas_per_sm=5, rhs_chunk=3, near_rhs_block=4)]
 
 
 @pytest.mark.parametrize("prec", [0, 2])
 def test_settings_do_not_change_the_product(pg, prec):
     import torch
     pr = pg.Problem(pg.Mesh(*pi.icosphere(3)), K, 4, root_side=2.0, precision=prec, max_nrhs=4)
-    assert pr.tuning == dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=4)
+    assert pr.tuning == dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=4, near_rhs_block=0)
     X = columns(pr.N, 5, 11)
     ref = pr.apply(X)
     torch.cuda.synchronize()
@@ -47,11 +49,11 @@ def test_settings_do_not_change_the_product(pg, prec):
 def test_tuning_rejects_out_of_range(pg):
     pr = pg.Problem(pg.Mesh(*pi.icosphere(2)), K, 3, root_side=2.0, max_nrhs=2)
     for bad in (dict(overlap=2), dict(near_ctas_per_sm=-1), dict(near_ctas_per_sm=33), dict(rhs_chunk=0),
-                dict(rhs_chunk=3)):
+                dict(rhs_chunk=3), dict(near_rhs_block=3), dict(near_rhs_block=16)):
         with pytest.raises(pg.PieError) as ei:
             pr.tuning = bad
         assert ei.value.code == 1
-    assert pr.tuning == dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=2)
+    assert pr.tuning == dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=2, near_rhs_block=0)
 
 
 def test_autotune_keeps_the_product(pg):
@@ -63,6 +65,7 @@ def test_autotune_keeps_the_product(pg):
     assert ms > 0
     assert best == pr.tuning
     assert best["overlap"] in (0, 1) and 0 <= best["near_ctas_per_sm"] <= 32 and 1 <= best["rhs_chunk"] <= 4
+    assert best["near_rhs_block"] in (0, 1, 2, 4, 8)
     assert torch.equal(pr.apply(X), ref)
 
 

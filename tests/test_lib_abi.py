@@ -95,7 +95,7 @@ def test_group_and_tuning_argument_checks_on_host(libpie):
     assert L.pie_group_apply(None, None, None, 1, None) == 1
     assert L.pie_group_info(None, None, None) == 1
     L.pie_group_destroy(None)
-    t = pg.Tuning(1, 2, 1)
+    t = pg.Tuning(1, 2, 1, 0)
     assert L.pie_problem_set_tuning(None, ctypes.byref(t)) == 1
     assert L.pie_problem_get_tuning(None, ctypes.byref(t)) == 1
     assert L.pie_problem_autotune(None, 1, 3, ctypes.byref(t), None, None) == 1
