@@ -203,14 +203,25 @@ __global__ void __launch_bounds__(kRedThreads) k_mupdate_norm(int64_t N, int nv,
   const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double nrm = 0;
   if (n < N) {
-    B r = 0, i = 0;
+    // four independent partial sums (vectors v = 4q + u), 16 loads in flight
+    B r[4] = {0, 0, 0, 0}, i[4] = {0, 0, 0, 0};
+    int v = 0;
 #pragma unroll 4
-    for (int v = 0; v < nv; ++v) {
-      C2<B> a = V[v * ldv + n], c = hs[v];
-      r += c.x * a.x - c.y * a.y;
-      i += c.x * a.y + c.y * a.x;
+    for (; v + 3 < nv; v += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const C2<B> a = V[(v + u) * ldv + n], c = hs[v + u];
+        r[u] += c.x * a.x - c.y * a.y;
+        i[u] += c.x * a.y + c.y * a.x;
+      }
     }
-    const C2<B> o = mk<B>(w[n].x - r, w[n].y - i);
+    for (; v < nv; ++v) {
+      const C2<B> a = V[v * ldv + n], c = hs[v];
+      r[0] += c.x * a.x - c.y * a.y;
+      i[0] += c.x * a.y + c.y * a.x;
+    }
+    const B rs = (r[0] + r[1]) + (r[2] + r[3]), is = (i[0] + i[1]) + (i[2] + i[3]);
+    const C2<B> o = mk<B>(w[n].x - rs, w[n].y - is);
     w[n] = o;
     nrm = double(o.x) * double(o.x) + double(o.y) * double(o.y);
   }
