@@ -124,7 +124,7 @@ __global__ void k_axs(int64_t N, double alpha, const C2<B>* __restrict__ x, C2<B
 // runs it against a chunk of kVecChunk vectors, so w is read once per chunk
 // and every thread has kVecChunk x kPerThread loads in flight; grid = (tiles,
 // vector chunks).
-constexpr int kPerThread = 8;
+constexpr int kPerThread = 16;
 constexpr int kTile = kRedThreads * kPerThread;
 constexpr int kVecChunk = 8;
 template <typename B>
