@@ -86,3 +86,31 @@ def test_solver_error_paths(pg):
     assert not st["converged"] and st["iterations"] == 50
     x, st = pr.solve(b, tol=1e-5)
     assert st["converged"]
+
+
+def test_low_frequency_solutions(pg):
+    """Low frequency (Section 2): the same mesh and tree at kR = 1e-2, 1e-4
+    and 1e-5 (MIXED) converge to 1e-6, keep the RCS within 0.1 dB of the Mie
+    series, and give the same RCS / k^4 (the Rayleigh scaling) to the far
+    part's accuracy.  (Below kR ~ 1e-5 on this mesh the diagonally scaled
+    system's condition, growing as 1/(k h)^2, meets the far part's rounding
+    nonlinearity and GMRES stops short of 1e-6, though the product keeps
+    its accuracy.)"""
+    from oracle import mie
+    xyz, tri = pi.icosphere(3)
+    mesh = pg.Mesh(xyz, tri)
+    rh = pi.bistatic_directions(91)
+    norm, its = [], []
+    for k in (1e-2, 1e-4, 1e-5):
+        pr = pg.Problem(mesh, k, 3, root_side=2.0, precision=pg.PIE_MIXED)
+        x, st = pr.solve(pr.rhs_planewave([0, 0, -1.0], [1.0, 0, 0]), tol=1e-6, maxit=3000, restart=300)
+        assert st["converged"], (k, st)
+        s = 4 * np.pi * np.sum(np.abs(pr.farfield(x, rh).cpu().numpy()) ** 2, axis=1)
+        sm = mie.rcs_eplane(k, 1.0, -rh[:, 2])
+        mask = sm > 1e-2 * sm.max()
+        assert np.max(np.abs(10 * np.log10(s[mask] / sm[mask]))) < 0.1, k
+        norm.append(s[mask] / k ** 4)
+        its.append(st["iterations"])
+    assert np.max(np.abs(norm[2] / norm[1] - 1)) < 1e-3
+    assert np.max(np.abs(norm[0] / norm[2] - 1)) < 2e-3    # plus O((kR)^2) at kR = 1e-2
+    print("iterations at kR = 1e-2, 1e-4, 1e-5:", its)
