@@ -119,56 +119,35 @@ __global__ void k_axs(int64_t N, double alpha, const C2<B>* __restrict__ x, C2<B
 }
 
 // partial[v][tile] = sum over the tile's entries of conj(V[v][n]) w[n]
-// (accumulated in the basis type per thread, then in double).  Pass 1 of a
-// fixed-order reduction.  A block takes one tile of w into registers and
-// runs it against a chunk of kVecChunk vectors, so w is read once per chunk
-// and every thread has kVecChunk x kPerThread loads in flight; grid = (tiles,
-// vector chunks).
-constexpr int kPerThread = 16;
-constexpr int kTile = kRedThreads * kPerThread;
-constexpr int kVecChunk = 8;
+// (accumulated in the basis type per lane, then in double).  Pass 1 of a
+// fixed-order reduction.  A block stages one tile of w in shared memory;
+// each warp runs it against its share of a chunk of kDotVecs vectors, every
+// lane streaming kDotTile / 32 entries of a vector before one warp
+// reduction; grid = (tiles, vector chunks).
+constexpr int kTile = 2048;
+constexpr int kDotVecs = 64;
 template <typename B>
 __global__ void __launch_bounds__(kRedThreads) k_mdot(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv,
                                                       const C2<B>* __restrict__ w, cd* __restrict__ partial) {
-  constexpr int NW = kRedThreads / 32;
-  __shared__ double sr[kVecChunk][NW], si[kVecChunk][NW];
-  const int v0 = blockIdx.y * kVecChunk, nvc = min(kVecChunk, nv - v0);
-  const int64_t n0 = int64_t(blockIdx.x) * kTile + threadIdx.x;
-  C2<B> wr[kPerThread];
-#pragma unroll
-  for (int k = 0; k < kPerThread; ++k) {
-    const int64_t n = n0 + int64_t(k) * kRedThreads;
-    wr[k] = n < N ? w[n] : mk<B>(0, 0);
-  }
+  __shared__ C2<B> ws[kTile];
+  const int64_t n0 = int64_t(blockIdx.x) * kTile;
+  const int lim = int(min(int64_t(kTile), N - n0));
+  for (int k = threadIdx.x; k < kTile; k += kRedThreads) ws[k] = k < lim ? w[n0 + k] : mk<B>(0, 0);
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int c = 0; c < kVecChunk; ++c) {
-    if (c >= nvc) break;
-    const C2<B>* vv = V + int64_t(v0 + c) * ldv;
+  for (int c = warp; c < kDotVecs; c += kRedThreads / 32) {
+    const int v = blockIdx.y * kDotVecs + c;
+    if (v >= nv) break;
+    const C2<B>* vv = V + int64_t(v) * ldv + n0;
     B ar = 0, ai = 0;
-#pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-      const int64_t n = n0 + int64_t(k) * kRedThreads;
-      if (n < N) {
-        const C2<B> a = vv[n], b = wr[k];
-        ar += a.x * b.x + a.y * b.y;
-        ai += a.x * b.y - a.y * b.x;
-      }
+#pragma unroll 8
+    for (int k = lane; k < lim; k += 32) {
+      const C2<B> a = vv[k], b = ws[k];
+      ar += a.x * b.x + a.y * b.y;
+      ai += a.x * b.y - a.y * b.x;
     }
     const double dr = warp_sum(double(ar)), di = warp_sum(double(ai));
-    if (lane == 0) {
-      sr[c][warp] = dr;
-      si[c][warp] = di;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < nvc) {
-    double tr = 0, ti = 0;
-    for (int k = 0; k < NW; ++k) {
-      tr += sr[threadIdx.x][k];
-      ti += si[threadIdx.x][k];
-    }
-    partial[int64_t(v0 + threadIdx.x) * gridDim.x + blockIdx.x] = mk<double>(tr, ti);
+    if (lane == 0) partial[int64_t(v) * gridDim.x + blockIdx.x] = mk<double>(dr, di);
   }
 }
 
@@ -336,8 +315,8 @@ struct EventPair {
 template <typename B>
 static pie_status dotc(Ctx& c, int nv, const C2<B>* V, const C2<B>* w, zc* out_host) {
   const unsigned tiles = unsigned((c.N + kTile - 1) / kTile);
-  k_mdot<B><<<dim3(tiles, unsigned((nv + kVecChunk - 1) / kVecChunk)), kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w,
-                                                                                              c.partial);
+  k_mdot<B><<<dim3(tiles, unsigned((nv + kDotVecs - 1) / kDotVecs)), kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w,
+                                                                                            c.partial);
   k_mdot_finish<<<nb_(int64_t(nv) * 32, 128), 128, 0, c.st>>>(nv, int(tiles), c.partial, c.hdev);
   pie_status s = cuda_check(cudaMemcpyAsync(out_host, c.hdev, sizeof(cd) * nv, cudaMemcpyDeviceToHost, c.st), "dot");
   if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "dot sync");
