@@ -1,9 +1,10 @@
 """Parity at full size, in the launch configuration bench.py times: the
-819,200-unknown sphere (icosphere n = 7), kR = 1e-3, 7 levels, PIE_MIXED,
-x = complex normal with seed 1234.  Sampled outputs are computed one by one
-by the oracle: full rows of the dense product (bar 1e-3, the accuracy of the
-approximate diagonalization) and near-part rows over the oracle's own tree
-(bar 1e-6, float pair moments)."""
+819,200-unknown sphere (icosphere n = 7), kR = 1e-3, 7 levels,
+x = complex normal with seed 1234, PIE_MIXED and then PIE_FP64.  Sampled
+outputs are computed one by one by the oracle: full rows of the dense
+product (bar 1e-3, the accuracy of the approximate diagonalization) and
+near-part rows over the oracle's own tree (bar 1e-6 with float pair
+moments, 1e-10 with double ones)."""
 import numpy as np
 import pytest
 
@@ -50,3 +51,13 @@ def test_bench_workload_sampled_rows():
         assert np.linalg.norm(yn[which][sl] - yno[sl]) <= 1e-6 * np.linalg.norm(yno[sl])
     print("full-size sampled rows: far+near", np.linalg.norm(y[which] - yo) / np.linalg.norm(yo),
           "near", np.linalg.norm(yn[which] - yno) / np.linalg.norm(yno))
+    # the plain FP64 form on the same rows: the same far part, the near part
+    # in complex double (its pair integrals then match the oracle's to 1e-12)
+    del pr
+    torch.cuda.empty_cache()
+    p64 = pg.Problem(pg.Mesh(xyz, tri), k, 7, root_side=2.0, precision=pg.PIE_FP64)
+    y64 = p64.apply(xd).cpu().numpy()
+    yn64 = p64.apply(xd, near_only=True).cpu().numpy()
+    for sl in (slice(0, 5), slice(5, 10)):
+        assert np.linalg.norm(y64[which][sl] - yo[sl]) <= 1e-3 * np.linalg.norm(yo[sl])
+        assert np.linalg.norm(yn64[which][sl] - yno[sl]) <= 1e-10 * np.linalg.norm(yno[sl])
