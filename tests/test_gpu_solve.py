@@ -93,9 +93,10 @@ def test_low_frequency_solutions(pg):
     and 1e-5 (MIXED) converge to 1e-6, keep the RCS within 0.1 dB of the Mie
     series, and give the same RCS / k^4 (the Rayleigh scaling) to the far
     part's accuracy.  (Below kR ~ 1e-5 on this mesh the diagonally scaled
-    system's condition, growing as 1/(k h)^2, meets the far part's rounding
-    nonlinearity and GMRES stops short of 1e-6, though the product keeps
-    its accuracy.)"""
+    system's spread, growing as 1/k, lifts the far part's rounding error
+    in the directions of its small singular values to the size of the
+    target residual, and GMRES stops short of 1e-6, though the product
+    keeps its accuracy.)"""
     from oracle import mie
     xyz, tri = pi.icosphere(3)
     mesh = pg.Mesh(xyz, tri)
