@@ -292,6 +292,15 @@ pie_status pie_farfield_adjoint(pie_problem* pr, const double* rhat, int64_t ndi
 pie_status pie_solve(pie_problem* pr, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
                      pie_solve_stats* stats, void* stream);
 
+/* pie_solve from the caller's x (N x nrhs, device, read as the initial
+ * guess and overwritten with the solution): the first residual is
+ * b - Z x instead of b.  Resumes an interrupted solve from a saved x (the
+ * operator is rebuilt deterministically from mesh, k0 and parameters), or
+ * starts a nearby right-hand side from a previous solution.  Same
+ * arguments, stopping test and errors as pie_solve. */
+pie_status pie_solve_guess(pie_problem* pr, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
+                           pie_solve_stats* stats, void* stream);
+
 /* Near-zone fields (Section 2).  The far zone needs J only; near-zone E needs
  * the charge density rho = i w eps0 n'.A - eps0 n'.grad'Phi, whose second
  * term solves Eq. (3): int_S (n'.grad'Phi) g = Phi^inc on S (the total scalar

@@ -65,7 +65,7 @@ EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_
            "pie_farfield_adjoint", "pie_apply_single_layer", "pie_solve_single_layer", "pie_rhs_potential",
            "pie_nearfield", "pie_problem_get_tuning", "pie_problem_set_tuning", "pie_problem_autotune",
            "pie_tune_levels", "pie_group_create", "pie_group_apply", "pie_group_info", "pie_group_destroy",
-           "pie_apply_levels", "pie_problem_quadrature", "pie_rhs_potentials"]
+           "pie_apply_levels", "pie_problem_quadrature", "pie_rhs_potentials", "pie_solve_guess"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -110,6 +110,7 @@ def lib():
         L.pie_profile_begin.argtypes = [vp, i32]
         L.pie_profile_end.argtypes = [vp, PD, P32]
         L.pie_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
+        L.pie_solve_guess.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
         L.pie_apply_levels.argtypes = [vp, vp, vp, ctypes.c_uint32, i32, i32, vp]
         PT = ctypes.POINTER(Tuning)
         L.pie_problem_get_tuning.argtypes = [vp, PT]
@@ -403,18 +404,21 @@ class Problem:
                                   rh.shape[0], ctypes.c_void_p(E.data_ptr()), nrhs, _stream(stream)))
         return E
 
-    def solve(self, b, tol=1e-6, maxit=1000, restart=100, stream=None):
-        """Restarted GMRES on Z x = b (pie_solve).  b [N] gives (x, stats);
-        b [nrhs, N] gives (x [nrhs, N], [stats per column])."""
+    def solve(self, b, tol=1e-6, maxit=1000, restart=100, stream=None, x0=None):
+        """Restarted GMRES on Z x = b (pie_solve; pie_solve_guess from the
+        initial guess x0 when given).  b [N] gives (x, stats); b [nrhs, N]
+        gives (x [nrhs, N], [stats per column])."""
         import torch
         b = _dense(b)
-        x = torch.zeros_like(b)
+        x = torch.zeros_like(b) if x0 is None else _dense(x0).clone()
+        assert x.shape == b.shape and x.dtype == b.dtype
         nrhs = 1 if b.dim() == 1 else b.shape[0]
         st = (SolveStats * max(nrhs, 1))()
         if nrhs == 0:
             return x, []
-        code = lib().pie_solve(self.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, tol,
-                               maxit, restart, st, _stream(stream))
+        fn = lib().pie_solve if x0 is None else lib().pie_solve_guess
+        code = fn(self.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, tol, maxit, restart,
+                  st, _stream(stream))
         if code not in (0, 8):
             _check(code)
         stats = [dict(iterations=s.iterations, rel_residual=s.rel_residual, seconds=s.seconds,

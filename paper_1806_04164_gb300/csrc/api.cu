@@ -416,8 +416,8 @@ pie_status pie_farfield(pie_problem* h, const void* x, const double* rhat, int64
   return PIE_OK;
 }
 
-pie_status pie_solve(pie_problem* h, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
-                     pie_solve_stats* stats, void* stream) {
+static pie_status solve_cols(pie_problem* h, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
+                             pie_solve_stats* stats, void* stream, bool guess) {
   if (!h || !b || !x || nrhs < 1 || !(tol > 0) || maxit < 1 || restart < 1) {
     set_error("pie_solve: invalid argument");
     return PIE_ERR_PARAM;
@@ -430,7 +430,7 @@ pie_status pie_solve(pie_problem* h, const void* b, void* x, int nrhs, double to
   std::string msg;
   for (int j = 0; j < nrhs; ++j) {
     pie_status s = solve(pr, static_cast<const char*>(b) + col * j, static_cast<char*>(x) + col * j, tol, maxit,
-                         restart, stats ? stats + j : nullptr, static_cast<cudaStream_t>(stream));
+                         restart, stats ? stats + j : nullptr, static_cast<cudaStream_t>(stream), guess);
     if (s == PIE_ERR_NOCONV || s == PIE_ERR_BREAKDOWN) {
       if (worst == PIE_OK) {
         worst = s;
@@ -442,6 +442,16 @@ pie_status pie_solve(pie_problem* h, const void* b, void* x, int nrhs, double to
   }
   if (worst != PIE_OK) set_error(msg);
   return worst;
+}
+
+pie_status pie_solve(pie_problem* h, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
+                     pie_solve_stats* stats, void* stream) {
+  return solve_cols(h, b, x, nrhs, tol, maxit, restart, stats, stream, false);
+}
+
+pie_status pie_solve_guess(pie_problem* h, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
+                           pie_solve_stats* stats, void* stream) {
+  return solve_cols(h, b, x, nrhs, tol, maxit, restart, stats, stream, true);
 }
 
 pie_status pie_problem_quadrature(const pie_problem* h, double* pts, double* wts) {

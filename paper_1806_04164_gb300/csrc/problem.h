@@ -141,7 +141,7 @@ pie_status nearzone(Problem& pr, const void* x, const void* rho, const double* p
 pie_status farfield_adjoint(Problem& pr, const double* rhat, int64_t ndir, const void* E, void* u,
                             cudaStream_t st);
 pie_status solve(Problem& pr, const void* b, void* x, double tol, int maxit, int restart,
-                 pie_solve_stats* stats, cudaStream_t st);
+                 pie_solve_stats* stats, cudaStream_t st, bool guess = false);
 
 pie_status cuda_check(cudaError_t e, const char* what);
 void* dalloc(Problem& pr, size_t bytes);

@@ -434,7 +434,7 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, Cycle& cy, double beta, double
 // reached (iterative refinement with a GMRES inner solver).
 template <typename B>
 static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double tol, int maxit, int restart,
-                          pie_solve_stats* stats, cudaStream_t st) {
+                          pie_solve_stats* stats, cudaStream_t st, bool guess = false) {
   auto t0 = std::chrono::steady_clock::now();
   const int64_t N = op == 0 ? pr.N : pr.T;
   const int m = std::min(restart, maxit);
@@ -473,8 +473,13 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
     k_diag_scale<double><<<nb_(N, 256), 256, 0, st>>>(N, pr.E, pr.nnz, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                       pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
                                                       pr.near_idx, pr.row_ptr, static_cast<const cd*>(pr.mom), w2e, d);
-  cudaMemsetAsync(x, 0, sizeof(cd) * N, st);
-  cudaMemcpyAsync(r, b, sizeof(cd) * N, cudaMemcpyDeviceToDevice, st);
+  if (guess) {  // start from the caller's x: r = b - Z x
+    if ((s = op_apply(c, x, wd)) != PIE_OK) return s;
+    k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, wd, r);
+  } else {
+    cudaMemsetAsync(x, 0, sizeof(cd) * N, st);
+    cudaMemcpyAsync(r, b, sizeof(cd) * N, cudaMemcpyDeviceToDevice, st);
+  }
   zc tmp[1];
   if ((s = dotc<double>(c, 1, b, b, tmp)) != PIE_OK) return s;
   const double bn = std::sqrt(tmp[0].real());
@@ -541,13 +546,13 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
 }
 
 pie_status solve(Problem& pr, const void* b, void* x, double tol, int maxit, int restart, pie_solve_stats* stats,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool guess) {
   if (pr.io_f32()) {
     set_error("pie_solve: needs a PIE_FP64 or PIE_MIXED problem (complex double vectors)");
     return PIE_ERR_PARAM;
   }
-  if (pr.par.precision == PIE_MIXED) return solve_t<float>(pr, 0, b, x, tol, maxit, restart, stats, st);
-  return solve_t<double>(pr, 0, b, x, tol, maxit, restart, stats, st);
+  if (pr.par.precision == PIE_MIXED) return solve_t<float>(pr, 0, b, x, tol, maxit, restart, stats, st, guess);
+  return solve_t<double>(pr, 0, b, x, tol, maxit, restart, stats, st, guess);
 }
 
 pie_status solve_single_layer(Problem& pr, const void* b, void* x, double tol, int maxit, int restart,

@@ -115,3 +115,22 @@ def test_low_frequency_solutions(pg):
     assert np.max(np.abs(norm[2] / norm[1] - 1)) < 1e-3
     assert np.max(np.abs(norm[0] / norm[2] - 1)) < 2e-3    # plus O((kR)^2) at kR = 1e-2
     print("iterations at kR = 1e-2, 1e-4, 1e-5:", its)
+
+
+def test_solve_resumes_from_a_guess(pg):
+    """pie_solve_guess: a solve stopped at 1e-3 and resumed from its x
+    reaches 1e-6 at about the cost of one solve; resuming from a converged
+    x takes no iteration and returns x unchanged."""
+    import torch
+    xyz, tri = pi.icosphere(3)
+    pr = pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=2.0, precision=pg.PIE_MIXED)
+    b = pr.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
+    x1, s1 = pr.solve(b, tol=1e-3, maxit=2000, restart=100)
+    assert s1["converged"] and s1["iterations"] > 0
+    x2, s2 = pr.solve(b, tol=1e-6, maxit=2000, restart=100, x0=x1)
+    assert s2["converged"] and s2["rel_residual"] <= 1e-6
+    xf, sf = pr.solve(b, tol=1e-6, maxit=2000, restart=100)
+    assert s1["iterations"] + s2["iterations"] <= 1.3 * sf["iterations"]
+    assert (torch.linalg.norm(x2 - xf) / torch.linalg.norm(xf)).item() < 1e-4
+    x3, s3 = pr.solve(b, tol=1e-6, maxit=2000, restart=100, x0=x2)
+    assert s3["iterations"] == 0 and torch.equal(x3, x2)
