@@ -102,6 +102,34 @@ def test_fp64_stages_match_oracle_mlfma(pg, mesh3, oracle3, L):
     assert rel(y, yo) < 1e-3
 
 
+def test_other_angular_grid_stages(pg, mesh3, dense3):
+    """An angular grid other than N_theta = 8 (N_theta = 6, P = 72, tau = 5,
+    kappa a = 0.06) takes the dense-filter interpolation / anterpolation
+    kernels instead of the factorised ones: patterns of every level and
+    component against the oracle MLFMA with the same parameters to 1e-12,
+    the product against it to its rounding, and against the dense matrix
+    to the accuracy of that parameter point."""
+    import torch
+    from oracle.mlfma import MLFMA
+    L = 4
+    M = MLFMA(*mesh3, K, L, tau=5, x=0.06, ntheta=6, side=2.0)
+    pr = pg.Problem(pg.Mesh(*mesh3), K, L, root_side=2.0, tau=5, kappa_a=0.06, ntheta=6)
+    assert pr.P == 72
+    x = pi.complex_normal(pr.N, 1234)
+    y = pr.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    yo, st = M.apply(x, stages=True)
+    for l in range(3, L + 1):
+        S, G = pr.stage(0, l), pr.stage(1, l)
+        for c in range(5):
+            assert rel(S[:, c], st["S"][l][:, c]) < 1e-12, ("S", l, c)
+            assert rel(G[:, c], st["G"][l][:, c]) < 1e-12, ("G", l, c)
+    assert rel(y, yo) < 1e-6
+    E = pr.E
+    yd = dense3 @ x
+    for sl in (slice(0, E), slice(E, None)):
+        assert rel(y[sl], yd[sl]) < 5e-3
+
+
 @pytest.mark.parametrize("prec", [0, 2])
 def test_product_matches_dense(pg, mesh3, dense3, prec):
     import torch
