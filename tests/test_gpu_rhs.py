@@ -72,3 +72,18 @@ def test_solve_and_farfield_columns(pg):
         x, st = pr.solve(B[j].contiguous(), tol=1e-6, maxit=2000, restart=100)
         assert torch.equal(X[j], x) and st["iterations"] == stats[j]["iterations"]
         assert torch.equal(E[j], pr.farfield(x, rh))
+
+
+def test_rhs_potential_of_eq3_matches_oracle(pg):
+    """pie_rhs_potential, the right-hand side <p_t, Phi^inc> of Eq. (3), is
+    the pulse part of the PIE right-hand side divided by -i w eps0."""
+    from oracle import constants as C
+    from oracle.excitation import rhs_planewave
+    from oracle.mesh import build_topology
+    xyz, tri = pi.icosphere(3)
+    top = build_topology(xyz, tri)
+    pr = pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=2.0, precision=pg.PIE_FP64)
+    kh, pol = [0.6, 0.0, -0.8], [0.8, 0.0, 0.6]
+    bq = pr.rhs_potential(kh, pol).cpu().numpy()
+    bo = rhs_planewave(top, K, kh, pol)[top.E:] / (-1j * C.omega_of_k(K) * C.EPS0)
+    assert rel(bq, bo) < 1e-12
