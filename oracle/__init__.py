@@ -23,6 +23,12 @@ Contents, each module citing the passage of Guer & Erguel (2017) it follows:
 * ``tree``       -- cubic-box oct-tree and one-box-buffer lists (Section 3).
 * ``mlfma``      -- aggregation / translation / disaggregation MVM (Section 3).
 * ``gmres``      -- restarted GMRES (Section 4).
+* ``levels``     -- the split of the product by the tree level that
+  translates each pair (Section 3), for the per-level error of the far part.
+* ``nearzone``   -- scattered field off the surface from J and the charge
+  density (Section 2).
+* ``search_asd`` -- the (tau, kappa a, N_theta) error search of Eqs. (4)-(5)
+  (a report generator).
 
 Parity status of each function is stated in its module header.
 """
