@@ -89,22 +89,31 @@ def assemble(top: Topology, k0: float, chunk=200000, pair_mask=None):
     return Z
 
 
-def rows(top: Topology, k0: float, which, x, pair_mask=None):
+def rows(top: Topology, k0: float, which, x, pair_mask=None, sources=None):
     """Selected entries of y = Z x computed row by row without storing Z.
 
     ``which`` holds indices into the mesh-order unknown vector.  Used to check
     sampled outputs of large problems one by one.  ``pair_mask(t, s)`` keeps
     only the source triangles s (array) paired with test triangle t for which
-    it returns True (e.g. the near part alone).
+    it returns True (e.g. the near part alone).  ``sources`` (optional) limits
+    the sum to those source triangles (mesh order): the rows' partial sums
+    over them.
     """
     E, T = top.E, top.T
     w = C.omega_of_k(k0)
-    geo = Geometry(top.xyz, top.tri)
-    idx, coef, div, dcp = _rwg_tables(top)
+    # geometry and RWG tables depend on the mesh only: built once per mesh
+    cache = top.__dict__.setdefault("_rows_cache", {})
+    if "geo" not in cache:
+        cache["geo"] = Geometry(top.xyz, top.tri)
+        cache["tables"] = _rwg_tables(top)
+    geo = cache["geo"]
+    tidx, tcoef, tdiv, tdcp = cache["tables"]
     x = np.asarray(x, np.complex128)
     xJ, xs = x[:E], x[E:]
     out = []
-    allsrc = np.arange(T)
+    allsrc = np.arange(T) if sources is None else np.asarray(sources, np.int64)
+    idx, coef, div, dcp = tidx[allsrc], tcoef[allsrc], tdiv[allsrc], tdcp[allsrc]
+    xs_src = xs[allsrc]
     for m in which:
         if m >= E:
             tests = [(m - E, None)]
@@ -112,27 +121,27 @@ def rows(top: Topology, k0: float, which, x, pair_mask=None):
             tests = [(int(top.edge_tri[m, 0]), m), (int(top.edge_tri[m, 1]), m)]
         acc = 0j
         for t, n in tests:
-            tarr = np.full(T, t)
+            tarr = np.full(allsrc.size, t)
             m0, mt, ms, mts = pair_moments(geo, k0, tarr, allsrc)
             if pair_mask is not None:
                 keep = pair_mask(t, allsrc)
                 m0, mt, ms, mts = m0 * keep, mt * keep[:, None], ms * keep[:, None], mts * keep
             if n is None:   # pulse test
-                acc += np.sum(w * w * C.EPS0 * m0 * xs)
+                acc += np.sum(w * w * C.EPS0 * m0 * xs_src)
                 for ks in range(3):
                     ns = idx[:, ks]
                     ok = ns >= 0
                     acc += np.sum(div[ok, ks] * m0[ok] * xJ[ns[ok]])
             else:           # RWG test
-                kt = int(np.nonzero(idx[t] == n)[0][0])
-                acc += np.sum(div[t, kt] * m0 * xs)
-                dt = dcp[t, kt]
+                kt = int(np.nonzero(tidx[t] == n)[0][0])
+                acc += np.sum(tdiv[t, kt] * m0 * xs_src)
+                dt = tdcp[t, kt]
                 for ks in range(3):
                     ns = idx[:, ks]
                     ok = ns >= 0
                     ds = dcp[ok, ks]
                     val = (mts[ok] + ms[ok] @ dt + np.einsum("pd,pd->p", mt[ok], ds)
                            + (ds @ dt) * m0[ok])
-                    acc += np.sum(C.MU0 * coef[t, kt] * coef[ok, ks] * val * xJ[ns[ok]])
+                    acc += np.sum(C.MU0 * tcoef[t, kt] * coef[ok, ks] * val * xJ[ns[ok]])
         out.append(acc)
     return np.array(out)

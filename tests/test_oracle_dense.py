@@ -137,3 +137,15 @@ def test_low_frequency_stability():
     for v in norm[1:]:
         assert np.max(np.abs(v - norm[-1])) <= 1e-6 * np.max(norm[-1])
     assert np.max(np.abs(norm[0] - norm[-1])) <= 1e-3 * np.max(norm[-1])   # O((kR)^2) at kR = 1e-2
+
+
+def test_rows_over_source_subsets_add_up(small):
+    """rows(..., sources=S) is the partial sum over S: two halves give the row."""
+    top, _ = small
+    x = pi.complex_normal(top.N, 9)
+    which = [0, 3, top.E, top.N - 1]
+    full = rows(top, 0.3, which, x)
+    half = np.arange(top.T) < top.T // 2
+    a = rows(top, 0.3, which, x, sources=np.nonzero(half)[0])
+    b = rows(top, 0.3, which, x, sources=np.nonzero(~half)[0])
+    assert np.allclose(a + b, full, rtol=1e-12, atol=0)
