@@ -301,6 +301,58 @@ pie_status pie_solve(pie_problem* pr, const void* b, void* x, int nrhs, double t
 pie_status pie_solve_guess(pie_problem* pr, const void* b, void* x, int nrhs, double tol, int maxit, int restart,
                            pie_solve_stats* stats, void* stream);
 
+/* Nested mixed-precision solve of Z x = b (Section 4 solves with GMRES; the
+ * inner operator is the same discrete PIE operator with its far part at an
+ * Eqs. (4)-(5) point whose rounding amplification complex float tolerates).
+ * Flexible GMRES (Saad 1993) on the outer problem's operator -- far part in
+ * FP64 -- right-preconditioned by one GMRES cycle on the inner problem's
+ * operator per outer step: z_j = (inner cycle from zero on v_j), product
+ * Z z_j with the outer operator.  Both operators are scaled by the outer
+ * problem's near-part diagonal (as pie_solve).  The outer Krylov vectors,
+ * the solution and the true residual b - Z x (recomputed with the outer
+ * operator at every outer restart) are complex double; the inner basis is
+ * complex float unless the inner problem is PIE_FP64.
+ *   outer: PIE_FP64 or PIE_MIXED problem; inner: any precision, built on the
+ *     same mesh (identical vertex and triangle arrays) at the same k0 (its
+ *     levels and (tau, kappa_a, ntheta) may differ);
+ *   b, x: device, N x nrhs complex double (column j at offset j*N), solved
+ *     column after column from x = 0;
+ *   stats: nrhs entries (host, may be NULL).
+ * Parameters (pie_nested_params):
+ *   tol: stopping test ||b - Z x|| / ||b|| <= tol with the outer operator;
+ *   maxit: bound on inner Arnoldi steps (inner products) per column;
+ *   inner_restart: steps of one inner cycle (1..1000);
+ *   inner_tol: an inner cycle stops once its residual has fallen by this
+ *     factor (0 < inner_tol < 1);
+ *   outer_restart: outer steps per restart (1..200); 0 = iterative
+ *     refinement (x += D z for the preconditioned scaled residual);
+ *   max_outer: bound on products with the outer operator per column.
+ * Synchronises the stream.  Returns PIE_OK when every column converged, else
+ * PIE_ERR_NOCONV of the first column that did not; PIE_ERR_PARAM (mismatched
+ * problems, PIE_FP32 outer problem, parameters out of range), PIE_ERR_OOM,
+ * PIE_ERR_NAN and PIE_ERR_CUDA stop at once. */
+typedef struct {
+  double tol;
+  int32_t maxit;
+  int32_t inner_restart;
+  double inner_tol;
+  int32_t outer_restart;
+  int32_t max_outer;
+} pie_nested_params;
+
+typedef struct {
+  int32_t inner_iterations;     /* inner Arnoldi steps (products with the inner operator) */
+  int32_t outer_iterations;     /* outer steps (inner cycles) */
+  int32_t outer_products;       /* products with the outer operator, true residuals included */
+  double rel_residual;          /* ||b - Z x|| / ||b|| with the outer operator, FP64 */
+  double seconds;               /* wall time of the solve */
+  double inner_product_seconds; /* part of `seconds` in inner products (CUDA events) */
+  double outer_product_seconds; /* part of `seconds` in outer products (CUDA events) */
+} pie_nested_stats;
+
+pie_status pie_solve_nested(pie_problem* outer, pie_problem* inner, const void* b, void* x, int nrhs,
+                            const pie_nested_params* params, pie_nested_stats* stats, void* stream);
+
 /* Near-zone fields (Section 2).  The far zone needs J only; near-zone E needs
  * the charge density rho = i w eps0 n'.A - eps0 n'.grad'Phi, whose second
  * term solves Eq. (3): int_S (n'.grad'Phi) g = Phi^inc on S (the total scalar

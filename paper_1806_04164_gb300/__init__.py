@@ -52,6 +52,17 @@ class Tuning(ctypes.Structure):
                     near_rhs_block=self.near_rhs_block)
 
 
+class NestedParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("inner_restart", ctypes.c_int32),
+                ("inner_tol", ctypes.c_double), ("outer_restart", ctypes.c_int32), ("max_outer", ctypes.c_int32)]
+
+
+class NestedStats(ctypes.Structure):
+    _fields_ = [("inner_iterations", ctypes.c_int32), ("outer_iterations", ctypes.c_int32),
+                ("outer_products", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("inner_product_seconds", ctypes.c_double), ("outer_product_seconds", ctypes.c_double)]
+
+
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("reorthogonalizations", ctypes.c_int32), ("product_seconds", ctypes.c_double)]
@@ -65,7 +76,8 @@ EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_
            "pie_farfield_adjoint", "pie_apply_single_layer", "pie_solve_single_layer", "pie_rhs_potential",
            "pie_nearfield", "pie_problem_get_tuning", "pie_problem_set_tuning", "pie_problem_autotune",
            "pie_tune_levels", "pie_group_create", "pie_group_apply", "pie_group_info", "pie_group_destroy",
-           "pie_apply_levels", "pie_problem_quadrature", "pie_rhs_potentials", "pie_solve_guess"]
+           "pie_apply_levels", "pie_problem_quadrature", "pie_rhs_potentials", "pie_solve_guess",
+           "pie_solve_nested"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -112,6 +124,8 @@ def lib():
         L.pie_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
         L.pie_solve_guess.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
         L.pie_apply_levels.argtypes = [vp, vp, vp, ctypes.c_uint32, i32, i32, vp]
+        L.pie_solve_nested.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(NestedParams),
+                                       ctypes.POINTER(NestedStats), vp]
         PT = ctypes.POINTER(Tuning)
         L.pie_problem_get_tuning.argtypes = [vp, PT]
         L.pie_problem_set_tuning.argtypes = [vp, PT]
@@ -424,6 +438,31 @@ class Problem:
         stats = [dict(iterations=s.iterations, rel_residual=s.rel_residual, seconds=s.seconds,
                       converged=s.rel_residual <= tol, reorthogonalizations=s.reorthogonalizations,
                       product_seconds=s.product_seconds) for s in st[:nrhs]]
+        return (x, stats[0]) if b.dim() == 1 else (x, stats)
+
+    def solve_nested(self, b, inner, tol=1e-6, maxit=20000, inner_restart=60, inner_tol=1e-2, outer_restart=20,
+                     max_outer=400, stream=None):
+        """Nested mixed-precision solve (pie_solve_nested): flexible GMRES on
+        this problem's operator, each outer step preconditioned by one GMRES
+        cycle on `inner` (a Problem on the same mesh and k0, typically
+        PIE_FP32 at a cheap (tau, kappa_a, ntheta)).  b [N] gives (x, stats);
+        b [nrhs, N] gives (x [nrhs, N], [stats per column])."""
+        import torch
+        b = _dense(b)
+        x = torch.zeros_like(b)
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        st = (NestedStats * max(nrhs, 1))()
+        if nrhs == 0:
+            return x, []
+        p = NestedParams(tol, maxit, inner_restart, inner_tol, outer_restart, max_outer)
+        code = lib().pie_solve_nested(self.handle, inner.handle, ctypes.c_void_p(b.data_ptr()),
+                                      ctypes.c_void_p(x.data_ptr()), nrhs, ctypes.byref(p), st, _stream(stream))
+        if code not in (0, 8):
+            _check(code)
+        stats = [dict(inner_iterations=s.inner_iterations, outer_iterations=s.outer_iterations,
+                      outer_products=s.outer_products, rel_residual=s.rel_residual, seconds=s.seconds,
+                      inner_product_seconds=s.inner_product_seconds, outer_product_seconds=s.outer_product_seconds,
+                      converged=s.rel_residual <= tol) for s in st[:nrhs]]
         return (x, stats[0]) if b.dim() == 1 else (x, stats)
 
     @property

@@ -454,6 +454,44 @@ pie_status pie_solve_guess(pie_problem* h, const void* b, void* x, int nrhs, dou
   return solve_cols(h, b, x, nrhs, tol, maxit, restart, stats, stream, true);
 }
 
+pie_status pie_solve_nested(pie_problem* ho, pie_problem* hi, const void* b, void* x, int nrhs,
+                            const pie_nested_params* np, pie_nested_stats* stats, void* stream) {
+  if (!ho || !hi || !b || !x || !np || nrhs < 1 || !(np->tol > 0) || np->maxit < 1 || np->inner_restart < 1 ||
+      np->inner_restart > 1000 || !(np->inner_tol > 0) || !(np->inner_tol < 1) || np->outer_restart < 0 ||
+      np->outer_restart > 200 || np->max_outer < 1) {
+    set_error("pie_solve_nested: invalid argument");
+    return PIE_ERR_PARAM;
+  }
+  Problem& po = ho->p;
+  Problem& pi = hi->p;
+  if (po.io_f32()) {
+    set_error("pie_solve_nested: the outer problem must be PIE_FP64 or PIE_MIXED (complex double vectors)");
+    return PIE_ERR_PARAM;
+  }
+  if (pi.N != po.N || pi.T != po.T || pi.E != po.E || pi.k0 != po.k0 || pi.mesh.tri != po.mesh.tri ||
+      pi.mesh.xyz != po.mesh.xyz) {
+    set_error("pie_solve_nested: inner and outer problems differ in mesh or k0");
+    return PIE_ERR_PARAM;
+  }
+  const size_t col = sizeof(cd) * size_t(po.N);
+  pie_status worst = PIE_OK;
+  std::string msg;
+  for (int j = 0; j < nrhs; ++j) {
+    pie_status s = solve_nested(po, pi, static_cast<const char*>(b) + col * j, static_cast<char*>(x) + col * j, *np,
+                                stats ? stats + j : nullptr, static_cast<cudaStream_t>(stream));
+    if (s == PIE_ERR_NOCONV) {
+      if (worst == PIE_OK) {
+        worst = s;
+        msg = g_err;
+      }
+      continue;
+    }
+    if (s != PIE_OK) return s;
+  }
+  if (worst != PIE_OK) set_error(msg);
+  return worst;
+}
+
 pie_status pie_problem_quadrature(const pie_problem* h, double* pts, double* wts) {
   if (!h) {
     set_error("pie_problem_quadrature: NULL problem");

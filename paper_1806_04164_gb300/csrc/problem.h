@@ -142,6 +142,8 @@ pie_status farfield_adjoint(Problem& pr, const double* rhat, int64_t ndir, const
                             cudaStream_t st);
 pie_status solve(Problem& pr, const void* b, void* x, double tol, int maxit, int restart,
                  pie_solve_stats* stats, cudaStream_t st, bool guess = false);
+pie_status solve_nested(Problem& outer, Problem& inner, const void* b, void* x, const pie_nested_params& np,
+                        pie_nested_stats* stats, cudaStream_t st);
 
 pie_status cuda_check(cudaError_t e, const char* what);
 void* dalloc(Problem& pr, size_t bytes);

@@ -233,6 +233,32 @@ __global__ void k_xupdate(int64_t N, int nv, const C2<B>* __restrict__ V, int64_
   x[n] = mk<double>(x[n].x + d[n] * r, x[n].y + d[n] * i);
 }
 
+// out = sum_v y[v] V[v] in complex double (no scaling, overwrites out).
+template <typename B>
+__global__ void k_combine(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv, const cd* __restrict__ y,
+                          cd* __restrict__ out) {
+  extern __shared__ cd yc[];
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) yc[v] = y[v];
+  __syncthreads();
+  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double r = 0, i = 0;
+  for (int v = 0; v < nv; ++v) {
+    C2<B> a = V[v * ldv + n];
+    cd c = yc[v];
+    r += c.x * double(a.x) - c.y * double(a.y);
+    i += c.x * double(a.y) + c.y * double(a.x);
+  }
+  out[n] = mk<double>(r, i);
+}
+
+// y = x converted between complex double and the Krylov basis type.
+template <typename A, typename B>
+__global__ void k_cvt(int64_t N, const C2<A>* __restrict__ x, C2<B>* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < N) y[i] = mk<B>(B(x[i].x), B(x[i].y));
+}
+
 // ---------------------------------------------------------------- host loop
 
 struct Work {
@@ -257,7 +283,7 @@ struct Work {
 
 // Shared scratch of the Krylov loop.
 struct Ctx {
-  Problem& pr;
+  Problem& pr;      // the problem whose operator the products apply
   cudaStream_t st;
   int op;           // 0: the PIE operator Z (N unknowns); 1: the single layer of Eq. (3) (T unknowns)
   int64_t N;
@@ -271,6 +297,8 @@ struct Ctx {
   bool pending = false;                      // ev0 / ev1 hold a product not yet counted
   double op_ms = 0;                          // time in operator products
   int reorth = 0;                            // second Gram-Schmidt passes
+  cf* u32 = nullptr;                         // operator input / output of a problem with
+  cf* w32 = nullptr;                         // complex-float vectors (PIE_FP32)
 };
 
 // Adds the last product's time (its events have completed: every product is
@@ -285,8 +313,9 @@ static void op_time_flush(Ctx& c) {
   c.pending = false;
 }
 
-// out = Z in, or out = S in for the single-layer operator of Eq. (3).
-static pie_status op_apply(Ctx& c, const cd* in, cd* out) {
+// out = Z in, or out = S in for the single-layer operator of Eq. (3)
+// (vectors in the io precision of the context's problem).
+static pie_status op_apply(Ctx& c, const void* in, void* out) {
   op_time_flush(c);
   if (c.ev0) cudaEventRecord(c.ev0, c.st);
   pie_status s = c.op == 0 ? apply_one(c.pr, in, out, c.st) : single_layer_one(c.pr, in, out, c.st);
@@ -295,6 +324,24 @@ static pie_status op_apply(Ctx& c, const cd* in, cd* out) {
     c.pending = true;
   }
   return s;
+}
+
+// out = D Op D in for a Krylov vector in type B; the product runs on complex
+// double vectors, or on complex float ones for a PIE_FP32 problem.
+template <typename B>
+static pie_status op_scaled(Ctx& c, const C2<B>* in, C2<B>* out) {
+  const int64_t N = c.N;
+  pie_status s;
+  if (c.pr.io_f32()) {
+    k_scale<B, float><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, in, c.u32);
+    if ((s = op_apply(c, c.u32, c.w32)) != PIE_OK) return s;
+    k_scale<float, B><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, c.w32, out);
+  } else {
+    k_scale<B, double><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, in, c.u);
+    if ((s = op_apply(c, c.u, c.wd)) != PIE_OK) return s;
+    k_scale<double, B><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, c.wd, out);
+  }
+  return PIE_OK;
 }
 
 struct EventPair {
@@ -349,9 +396,71 @@ struct Cycle {
   std::vector<zc> H, cs, sn, g, h, h2;
   int m;
   explicit Cycle(int m_) : H(size_t(m_ + 1) * m_), cs(m_), sn(m_), g(m_ + 1), h(m_ + 1), h2(m_ + 1), m(m_) {}
+  void reset(double beta) {
+    std::fill(H.begin(), H.end(), zc(0));
+    std::fill(g.begin(), g.end(), zc(0));
+    g[0] = beta;
+  }
 };
 
-// One GMRES cycle (no restart) on the scaled operator D Z D, x0 = 0, with
+// Classical Gram-Schmidt of w (basis slot j + 1) against V[0..j]; a second
+// pass only when the first one cancelled most of w (Daniel-Gragg-Kaufman-
+// Stewart criterion).  One reduction gives (v_i, w) for i <= j and (w, w);
+// the update returns the new norm.  cy.h[0..j] gets the projections, *hn
+// the norm of the orthogonalised w.
+template <typename B>
+static pie_status orthogonalize(Ctx& c, const C2<B>* V, int j, C2<B>* w, Cycle& cy, double* hn) {
+  pie_status s;
+  if ((s = dotc<B>(c, j + 2, V, w, cy.h.data())) != PIE_OK) return s;
+  const double wn0 = std::sqrt(cy.h[j + 1].real());
+  if ((s = update_norm<B>(c, j + 1, V, w, hn)) != PIE_OK) return s;
+  if (*hn < 0.7 * wn0) {
+    ++c.reorth;
+    if ((s = dotc<B>(c, j + 1, V, w, cy.h2.data())) != PIE_OK) return s;
+    if ((s = update_norm<B>(c, j + 1, V, w, hn)) != PIE_OK) return s;
+    for (int i = 0; i <= j; ++i) cy.h[i] += cy.h2[i];
+  }
+  for (int i = 0; i <= j; ++i)
+    if (!std::isfinite(cy.h[i].real()) || !std::isfinite(cy.h[i].imag()) || !std::isfinite(*hn)) {
+      set_error("pie_solve: non-finite Arnoldi coefficient");
+      return PIE_ERR_NAN;
+    }
+  return PIE_OK;
+}
+
+// Column j of the Hessenberg matrix (cy.h[0..j] and hn below the diagonal):
+// previous rotations, then a new one G = [[conj c, conj s], [-s, c]].
+// Returns the rotated diagonal entry.
+static double hessenberg_column(Cycle& cy, int j, double hn) {
+  const int m = cy.m;
+  for (int i = 0; i <= j; ++i) cy.H[size_t(i) * m + j] = cy.h[i];
+  for (int i = 0; i < j; ++i) {
+    zc a = cy.H[size_t(i) * m + j], b = cy.H[size_t(i + 1) * m + j];
+    cy.H[size_t(i) * m + j] = std::conj(cy.cs[i]) * a + std::conj(cy.sn[i]) * b;
+    cy.H[size_t(i + 1) * m + j] = -cy.sn[i] * a + cy.cs[i] * b;
+  }
+  zc a = cy.H[size_t(j) * m + j];
+  double den = std::sqrt(std::norm(a) + hn * hn);
+  cy.cs[j] = a / den;
+  cy.sn[j] = zc(hn / den);
+  cy.H[size_t(j) * m + j] = den;
+  cy.g[j + 1] = -cy.sn[j] * cy.g[j];
+  cy.g[j] = std::conj(cy.cs[j]) * cy.g[j];
+  return den;
+}
+
+// y = R^{-1} g over the first j columns (back substitution).
+static void back_substitute(const Cycle& cy, int j, std::vector<zc>& y) {
+  const int m = cy.m;
+  y.assign(j, zc(0));
+  for (int i = j - 1; i >= 0; --i) {
+    zc acc = cy.g[i];
+    for (int k = i + 1; k < j; ++k) acc -= cy.H[size_t(i) * m + k] * y[k];
+    y[i] = acc / cy.H[size_t(i) * m + i];
+  }
+}
+
+// One GMRES cycle (no restart) on the scaled operator D Op D, x0 = 0, with
 // V[0] = D r / ||D r|| given: Arnoldi up to m steps or until the rotated
 // residual falls below stop_abs.  On return y (host) holds the coefficients
 // and j the number of steps.
@@ -361,50 +470,16 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, Cycle& cy, double beta, double
   const int64_t N = c.N;
   const int m = cy.m;
   pie_status s = PIE_OK;
-  std::fill(cy.H.begin(), cy.H.end(), zc(0));
-  std::fill(cy.g.begin(), cy.g.end(), zc(0));
-  cy.g[0] = beta;
+  cy.reset(beta);
   int j = 0;
   breakdown = false;
   for (; j < m && j < max_steps; ++j) {
-    const C2<B>* vj = V + size_t(j) * N;
-    // the new vector is built in its own basis slot: w = D Z D v_j
+    // the new vector is built in its own basis slot: w = D Op D v_j
     C2<B>* w = V + size_t(j + 1) * N;
-    k_scale<B, double><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, vj, c.u);
-    if ((s = op_apply(c, c.u, c.wd)) != PIE_OK) return s;
-    k_scale<double, B><<<nb_(N, 256), 256, 0, c.st>>>(N, c.d, c.wd, w);
-    // classical Gram-Schmidt; a second pass only when the first one cancelled
-    // most of w (Daniel-Gragg-Kaufman-Stewart criterion).  One reduction
-    // gives (v_i, w) for i <= j and (w, w); the update returns the new norm.
-    if ((s = dotc<B>(c, j + 2, V, w, cy.h.data())) != PIE_OK) return s;
-    const double wn0 = std::sqrt(cy.h[j + 1].real());
+    if ((s = op_scaled<B>(c, V + size_t(j) * N, w)) != PIE_OK) return s;
     double hn = 0;
-    if ((s = update_norm<B>(c, j + 1, V, w, &hn)) != PIE_OK) return s;
-    if (hn < 0.7 * wn0) {
-      ++c.reorth;
-      if ((s = dotc<B>(c, j + 1, V, w, cy.h2.data())) != PIE_OK) return s;
-      if ((s = update_norm<B>(c, j + 1, V, w, &hn)) != PIE_OK) return s;
-      for (int i = 0; i <= j; ++i) cy.h[i] += cy.h2[i];
-    }
-    for (int i = 0; i <= j; ++i)
-      if (!std::isfinite(cy.h[i].real()) || !std::isfinite(cy.h[i].imag()) || !std::isfinite(hn)) {
-        set_error("pie_solve: non-finite Arnoldi coefficient");
-        return PIE_ERR_NAN;
-      }
-    for (int i = 0; i <= j; ++i) cy.H[size_t(i) * m + j] = cy.h[i];
-    // previous rotations, then a new one: G = [[conj c, conj s], [-s, c]]
-    for (int i = 0; i < j; ++i) {
-      zc a = cy.H[size_t(i) * m + j], b = cy.H[size_t(i + 1) * m + j];
-      cy.H[size_t(i) * m + j] = std::conj(cy.cs[i]) * a + std::conj(cy.sn[i]) * b;
-      cy.H[size_t(i + 1) * m + j] = -cy.sn[i] * a + cy.cs[i] * b;
-    }
-    zc a = cy.H[size_t(j) * m + j];
-    double den = std::sqrt(std::norm(a) + hn * hn);
-    cy.cs[j] = a / den;
-    cy.sn[j] = zc(hn / den);
-    cy.H[size_t(j) * m + j] = den;
-    cy.g[j + 1] = -cy.sn[j] * cy.g[j];
-    cy.g[j] = std::conj(cy.cs[j]) * cy.g[j];
+    if ((s = orthogonalize<B>(c, V, j, w, cy, &hn)) != PIE_OK) return s;
+    const double den = hessenberg_column(cy, j, hn);
     ++steps_done;
     if (hn <= 1e-14 * den) {
       breakdown = true;
@@ -417,14 +492,29 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, Cycle& cy, double beta, double
       break;
     }
   }
-  y.assign(j, zc(0));
-  for (int i = j - 1; i >= 0; --i) {
-    zc acc = cy.g[i];
-    for (int k = i + 1; k < j; ++k) acc -= cy.H[size_t(i) * m + k] * y[k];
-    y[i] = acc / cy.H[size_t(i) * m + i];
-  }
+  back_substitute(cy, j, y);
   j_out = j;
   return cuda_check(cudaGetLastError(), "arnoldi");
+}
+
+// |Z_ii|^{-1/2} (op 0) or |S_tt|^{-1/2} (op 1) from the near pair moments.
+static void diag_scaling(Problem& pr, int op, int64_t N, double* d, cudaStream_t st) {
+  const double w2e = pr.w * pr.w * eps0();
+  if (op == 1) {
+    if (pr.near_f32())
+      k_diag_single<float><<<nb_(N, 256), 256, 0, st>>>(N, pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
+                                                        pr.near_idx, pr.row_ptr, static_cast<const cf*>(pr.mom), d);
+    else
+      k_diag_single<double><<<nb_(N, 256), 256, 0, st>>>(N, pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
+                                                         pr.near_idx, pr.row_ptr, static_cast<const cd*>(pr.mom), d);
+  } else if (pr.near_f32())
+    k_diag_scale<float><<<nb_(N, 256), 256, 0, st>>>(N, pr.E, pr.nnz, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                     pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx,
+                                                     pr.row_ptr, static_cast<const cf*>(pr.mom), w2e, d);
+  else
+    k_diag_scale<double><<<nb_(N, 256), 256, 0, st>>>(N, pr.E, pr.nnz, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
+                                                      pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
+                                                      pr.near_idx, pr.row_ptr, static_cast<const cd*>(pr.mom), w2e, d);
 }
 
 // Restarted GMRES with the Krylov basis in type B (double for PIE_FP64,
@@ -457,22 +547,7 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
   }
   const cd* b = static_cast<const cd*>(bv);
   cd* x = static_cast<cd*>(xv);
-  const double w2e = pr.w * pr.w * eps0();
-  if (op == 1) {
-    if (pr.near_f32())
-      k_diag_single<float><<<nb_(N, 256), 256, 0, st>>>(N, pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                        pr.near_idx, pr.row_ptr, static_cast<const cf*>(pr.mom), d);
-    else
-      k_diag_single<double><<<nb_(N, 256), 256, 0, st>>>(N, pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                         pr.near_idx, pr.row_ptr, static_cast<const cd*>(pr.mom), d);
-  } else if (pr.near_f32())
-    k_diag_scale<float><<<nb_(N, 256), 256, 0, st>>>(N, pr.E, pr.nnz, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
-                                                     pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx,
-                                                     pr.row_ptr, static_cast<const cf*>(pr.mom), w2e, d);
-  else
-    k_diag_scale<double><<<nb_(N, 256), 256, 0, st>>>(N, pr.E, pr.nnz, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
-                                                      pr.inv_perm, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                      pr.near_idx, pr.row_ptr, static_cast<const cd*>(pr.mom), w2e, d);
+  diag_scaling(pr, op, N, d, st);
   if (guess) {  // start from the caller's x: r = b - Z x
     if ((s = op_apply(c, x, wd)) != PIE_OK) return s;
     k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, wd, r);
@@ -486,6 +561,7 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
   int it = 0;
   double rel = bn == 0 ? 0.0 : 1.0;
   pie_status result = bn == 0 ? PIE_OK : PIE_ERR_NOCONV;
+  if (bn == 0) cudaMemsetAsync(x, 0, sizeof(cd) * N, st);  // b = 0: the solution is x = 0, whatever the guess
   Cycle cy(m);
   std::vector<zc> y;
   while (result != PIE_OK && it < maxit) {
@@ -563,6 +639,166 @@ pie_status solve_single_layer(Problem& pr, const void* b, void* x, double tol, i
   }
   if (pr.par.precision == PIE_MIXED) return solve_t<float>(pr, 1, b, x, tol, maxit, restart, stats, st);
   return solve_t<double>(pr, 1, b, x, tol, maxit, restart, stats, st);
+}
+
+// ---------------------------------------------------------------- nested solve
+
+// Flexible GMRES (Saad 1993) on the outer operator D Z D, right-preconditioned
+// by a few GMRES steps on the inner operator D Z' D: z_j = M_j(v_j) is one
+// inner cycle from zero on the outer Krylov vector v_j, the outer product is
+// w = D Z D z_j, and the solution is x += D sum_j y_j z_j.  Z' is the same
+// discrete PIE operator with its far part at (tau, kappa a, N_theta) chosen for
+// complex float (Eqs. (4)-(5): the rounding amplification of the scaled
+// Hankel terms is small there), so its products are far cheaper than those of
+// the outer FP64-far operator; the outer operator, the solution and the true
+// residual at every restart stay in complex double.  outer_restart = 0 is
+// plain iterative refinement: x += D z with z = M(D r / ||D r||) ||D r||.
+template <typename Bi>
+static pie_status nested_t(Problem& po, Problem& pi, const cd* b, cd* x, const pie_nested_params& np,
+                           pie_nested_stats* stats, cudaStream_t st) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t N = po.N;
+  const int mi = np.inner_restart;
+  const int mo = std::max(np.outer_restart, 1);
+  const bool ir = np.outer_restart == 0;
+  const int mmax = std::max(mi, mo);
+  pie_status s = PIE_OK;
+  Work wk;
+  double* d = wk.get<double>(N, s);
+  C2<Bi>* Vi = wk.get<C2<Bi>>(size_t(N) * (mi + 1), s);  // inner basis
+  cd* Vo = wk.get<cd>(size_t(N) * (mo + 1), s);           // outer basis
+  cd* Zo = wk.get<cd>(size_t(N) * mo, s);                 // preconditioned outer vectors
+  cd* u = wk.get<cd>(N, s);
+  cd* wd = wk.get<cd>(N, s);
+  cd* r = wk.get<cd>(N, s);
+  cf* u32 = pi.io_f32() ? wk.get<cf>(N, s) : nullptr;
+  cf* w32 = pi.io_f32() ? wk.get<cf>(N, s) : nullptr;
+  cd* partial = wk.get<cd>(std::max(size_t((N + kTile - 1) / kTile) * (mmax + 2), size_t(nb_(N, kRedThreads))), s);
+  cd* hdev = wk.get<cd>(mmax + 3, s);
+  if (s != PIE_OK) return s;
+  EventPair evo, evi;
+  Ctx co{po, st, 0, N, d, u, wd, partial, hdev};
+  Ctx ci{pi, st, 0, N, d, u, wd, partial, hdev};
+  co.hcap = ci.hcap = mmax + 3;
+  ci.u32 = u32;
+  ci.w32 = w32;
+  if (evo.a && evo.b) co.ev0 = evo.a, co.ev1 = evo.b;
+  if (evi.a && evi.b) ci.ev0 = evi.a, ci.ev1 = evi.b;
+  diag_scaling(po, 0, N, d, st);
+  cudaMemsetAsync(x, 0, sizeof(cd) * N, st);
+  cudaMemcpyAsync(r, b, sizeof(cd) * N, cudaMemcpyDeviceToDevice, st);
+  zc tmp[1];
+  if ((s = dotc<double>(co, 1, b, b, tmp)) != PIE_OK) return s;
+  const double bn = std::sqrt(tmp[0].real());
+  int inner_steps = 0, outer_steps = 0, outer_products = 0;
+  double rel = bn == 0 ? 0.0 : 1.0;
+  pie_status result = bn == 0 ? PIE_OK : PIE_ERR_NOCONV;
+  Cycle cyi(mi), cyo(mo);
+  std::vector<zc> y, yo;
+  // z = M(v): one inner GMRES cycle on D Z' D from zero for the unit vector v
+  // (complex double), at most mi steps, stopping at relative residual
+  // inner_tol; z in complex double.
+  auto precondition = [&](const cd* v, cd* z) -> pie_status {
+    k_cvt<double, Bi><<<nb_(N, 256), 256, 0, st>>>(N, v, Vi);
+    int j = 0;
+    bool brk = false;
+    pie_status e = arnoldi_cycle<Bi>(ci, Vi, cyi, 1.0, np.inner_tol, std::min(mi, np.maxit - inner_steps), j, y,
+                                     brk, inner_steps);
+    if (e != PIE_OK) return e;
+    if (j == 0) return cuda_check(cudaMemcpyAsync(z, v, sizeof(cd) * N, cudaMemcpyDeviceToDevice, st), "copy");
+    if ((e = to_dev(ci, y, j)) != PIE_OK) return e;
+    k_combine<Bi><<<nb_(N, 256), 256, sizeof(cd) * j, st>>>(N, j, Vi, N, hdev, z);
+    return cuda_check(cudaGetLastError(), "precondition");
+  };
+  while (result != PIE_OK && inner_steps < np.maxit && outer_products < np.max_outer) {
+    if ((s = dotc<double>(co, 1, r, r, tmp)) != PIE_OK) return s;
+    rel = std::sqrt(tmp[0].real()) / bn;
+    if (!std::isfinite(rel)) {
+      set_error("pie_solve_nested: non-finite residual");
+      return PIE_ERR_NAN;
+    }
+    if (rel <= np.tol) {
+      result = PIE_OK;
+      break;
+    }
+    // first outer vector: the scaled residual D r, normalised
+    k_scale<double, double><<<nb_(N, 256), 256, 0, st>>>(N, d, r, Vo);
+    if ((s = dotc<double>(co, 1, Vo, Vo, tmp)) != PIE_OK) return s;
+    const double beta = std::sqrt(tmp[0].real());
+    k_axs<double><<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / beta, Vo, Vo);
+    int j = 0;
+    if (ir) {
+      // x += beta D M(v0)
+      if ((s = precondition(Vo, Zo)) != PIE_OK) return s;
+      ++outer_steps;
+      yo.assign(1, zc(beta));
+      j = 1;
+    } else {
+      const double dbn = beta / rel;  // scale of ||D b||
+      cyo.reset(beta);
+      bool brk = false;
+      for (; j < mo && inner_steps < np.maxit && outer_products < np.max_outer; ++j) {
+        cd* zj = Zo + size_t(j) * N;
+        if ((s = precondition(Vo + size_t(j) * N, zj)) != PIE_OK) return s;
+        cd* w = Vo + size_t(j + 1) * N;
+        if ((s = op_scaled<double>(co, zj, w)) != PIE_OK) return s;
+        ++outer_products;
+        double hn = 0;
+        if ((s = orthogonalize<double>(co, Vo, j, w, cyo, &hn)) != PIE_OK) return s;
+        const double den = hessenberg_column(cyo, j, hn);
+        ++outer_steps;
+        if (hn <= 1e-14 * den) {
+          brk = true;
+          ++j;
+          break;
+        }
+        k_axs<double><<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / hn, w, w);
+        if (std::abs(cyo.g[j + 1]) <= 0.5 * np.tol * dbn) {
+          ++j;
+          break;
+        }
+      }
+      (void)brk;
+      back_substitute(cyo, j, yo);
+    }
+    // x += D (sum_j y_j z_j), complex double
+    if ((s = to_dev(co, yo, j)) != PIE_OK) return s;
+    k_xupdate<double><<<nb_(N, 256), 256, sizeof(cd) * std::max(j, 1), st>>>(N, j, Zo, N, hdev, d, x);
+    // true residual r = b - Z x with the outer operator
+    if ((s = op_apply(co, x, wd)) != PIE_OK) return s;
+    ++outer_products;
+    k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, wd, r);
+    if ((s = cuda_check(cudaGetLastError(), "nested launch")) != PIE_OK) return s;
+  }
+  if (result != PIE_OK) {
+    if ((s = dotc<double>(co, 1, r, r, tmp)) != PIE_OK) return s;
+    rel = std::sqrt(tmp[0].real()) / bn;
+    if (rel <= np.tol)
+      result = PIE_OK;
+    else
+      set_error("pie_solve_nested: tolerance not reached within maxit inner steps / max_outer outer products");
+  }
+  if ((s = cuda_check(cudaStreamSynchronize(st), "nested sync")) != PIE_OK) return s;
+  op_time_flush(co);
+  op_time_flush(ci);
+  if (stats) {
+    stats->inner_iterations = inner_steps;
+    stats->outer_iterations = outer_steps;
+    stats->outer_products = outer_products;
+    stats->rel_residual = rel;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    stats->inner_product_seconds = ci.op_ms * 1e-3;
+    stats->outer_product_seconds = co.op_ms * 1e-3;
+  }
+  return result;
+}
+
+pie_status solve_nested(Problem& outer, Problem& inner, const void* b, void* x, const pie_nested_params& np,
+                        pie_nested_stats* stats, cudaStream_t st) {
+  // the inner Krylov basis is complex float unless the inner operator is FP64
+  if (inner.par.precision == PIE_FP64)
+    return nested_t<double>(outer, inner, static_cast<const cd*>(b), static_cast<cd*>(x), np, stats, st);
+  return nested_t<float>(outer, inner, static_cast<const cd*>(b), static_cast<cd*>(x), np, stats, st);
 }
 
 }  // namespace pie
