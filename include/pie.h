@@ -64,9 +64,15 @@ typedef enum { PIE_C128 = 0, PIE_C64 = 1 } pie_dtype;
  *  PIE_FP64  everything in complex double (inputs/outputs PIE_C128);
  *  PIE_FP32  near and far parts in complex float (inputs/outputs PIE_C64);
  *  PIE_MIXED near part in complex float (pair moments stored as float),
- *            far part in complex double (inputs/outputs PIE_C128).
+ *            far part in complex double (inputs/outputs PIE_C128);
+ *  PIE_FP32H as PIE_FP32, with the near pair moments stored in IEEE half
+ *            precision, each of the eight moment planes scaled by its own
+ *            power of two (largest magnitude in [2^14, 2^15)) and converted
+ *            back to float in the product: half the near-part bytes, a
+ *            fixed relative rounding of ~2.4e-4 per moment.  Meant for the
+ *            inner operator of pie_solve_nested.
  * Setup (pair integrals, translation operators, filters) is always FP64. */
-typedef enum { PIE_FP64 = 0, PIE_FP32 = 1, PIE_MIXED = 2 } pie_precision;
+typedef enum { PIE_FP64 = 0, PIE_FP32 = 1, PIE_MIXED = 2, PIE_FP32H = 3 } pie_precision;
 
 typedef struct pie_mesh pie_mesh;
 typedef struct pie_problem pie_problem;

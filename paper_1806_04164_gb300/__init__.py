@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libpie.so")
 
-PIE_FP64, PIE_FP32, PIE_MIXED = 0, 1, 2
+PIE_FP64, PIE_FP32, PIE_MIXED, PIE_FP32H = 0, 1, 2, 3
 PIE_C128, PIE_C64 = 0, 1
 STATUS = {0: "PIE_OK", 1: "PIE_ERR_PARAM", 2: "PIE_ERR_NONMANIFOLD", 3: "PIE_ERR_DEGENERATE",
           4: "PIE_ERR_ORIENTATION", 5: "PIE_ERR_OOM", 6: "PIE_ERR_CUDA", 7: "PIE_ERR_LEAF",
@@ -209,7 +209,7 @@ class Problem:
         self.near_pairs = info.near_pairs
         self.device_bytes = info.device_bytes
         self.leaf_size = info.leaf_size
-        self.dtype_code = PIE_C64 if precision == PIE_FP32 else PIE_C128
+        self.dtype_code = PIE_C64 if precision in (PIE_FP32, PIE_FP32H) else PIE_C128
 
     @property
     def torch_dtype(self):

@@ -5,6 +5,8 @@
 #include <new>
 #include <string>
 
+#include <cuda_fp16.h>
+
 #include "handles.h"
 
 namespace pie {
@@ -96,7 +98,7 @@ pie_status pie_problem_create(const pie_mesh* m, double k0, const pie_params* pa
   *out = nullptr;
   if (!(k0 > 0) || par->levels < 3 || par->levels > 21 || par->tau < 0 || par->tau > 30 || par->ntheta < 1 ||
       2 * par->ntheta * par->ntheta > 1024 || (par->ntheta & 1) || !(par->kappa_a > 0) || par->precision < 0 ||
-      par->precision > 2 || par->max_nrhs < 1 || par->max_nrhs > 1024) {
+      par->precision > 3 || par->max_nrhs < 1 || par->max_nrhs > 1024) {
     set_error("pie_problem_create: parameter out of range");
     return PIE_ERR_PARAM;
   }
@@ -364,6 +366,17 @@ pie_status pie_problem_stage(pie_problem* h, int which, int level, double* out, 
     src = pr.mom;
     n = size_t(pr.nnz) * kMom;
     f32 = pr.near_f32();
+    if (pr.near_h16()) {  // half pairs times the plane scales
+      std::vector<__half2> tmp(n);
+      s = cuda_check(cudaMemcpy(tmp.data(), src, n * sizeof(__half2), cudaMemcpyDeviceToHost), "stage copy");
+      if (s != PIE_OK) return s;
+      for (size_t i = 0; i < n; ++i) {
+        const float sc = pr.mom_scale[i / size_t(pr.nnz)];
+        out[2 * i] = double(__low2float(tmp[i])) * sc;
+        out[2 * i + 1] = double(__high2float(tmp[i])) * sc;
+      }
+      return PIE_OK;
+    }
   } else if (which == 5 || which == 6) {
     src = which == 5 ? pr.Pi : pr.M;
     n = size_t(pr.T) * (pr.P / 2) * (which == 5 ? 1 : 3);

@@ -56,14 +56,16 @@ __global__ void k_coef(int64_t T, int64_t E, const C2<Rio>* __restrict__ x, cons
 // triangles of the neighbouring leaf boxes (contiguous in tree order), whose
 // eight pair moments are stored plane by plane ([8][nnz]), so a warp reads
 // 32 consecutive entries of each plane (measured faster than per-pair
-// records with vector loads).  Writes pot[t] (initialises it).
-template <typename Rm, typename Rio, int RB = 1>
+// records with vector loads).  Writes pot[t] (initialises it).  H16: the
+// moments come from momh (half pairs, PIE_FP32H) times their plane's scale.
+template <typename Rm, typename Rio, int RB = 1, bool H16 = false>
 __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int32_t* __restrict__ leaf_of,
                                               const int32_t* __restrict__ leaf_start,
                                               const int32_t* __restrict__ near_ptr,
                                               const int32_t* __restrict__ near_idx,
                                               const int32_t* __restrict__ near_off,
                                               const int64_t* __restrict__ row_ptr, const C2<Rm>* __restrict__ mom,
+                                              const __half2* __restrict__ momh, MomScale msc,
                                               const C2<Rm>* __restrict__ coef, Rm mu0, C2<Rio>* __restrict__ pot,
                                               int nrhs = 1, int64_t sc = 0, int64_t sp = 0) {
   const int lane = threadIdx.x & 31;
@@ -90,10 +92,19 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
       while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
       const int64_t s = leaf_start[near_idx[qi]] + (j - near_off[qi]);
       const int64_t ee = e0 + j;
-      C2<Rm> m0 = mom[ee];
-      C2<Rm> mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
-      C2<Rm> ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
-      C2<Rm> mts = mom[7 * nnz + ee];
+      C2<Rm> m0, mt0, mt1, mt2, ms0, ms1, ms2, mts;
+      if constexpr (H16) {
+        auto ld = [&](int q) {
+          const float2 v = __half22float2(momh[q * nnz + ee]);
+          return mk<Rm>(Rm(v.x * msc.s[q]), Rm(v.y * msc.s[q]));
+        };
+        m0 = ld(0), mt0 = ld(1), mt1 = ld(2), mt2 = ld(3), ms0 = ld(4), ms1 = ld(5), ms2 = ld(6), mts = ld(7);
+      } else {
+        m0 = mom[ee];
+        mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
+        ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
+        mts = mom[7 * nnz + ee];
+      }
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         if (r0 + r >= nrhs) break;
@@ -145,11 +156,13 @@ __device__ __forceinline__ int antipode(int q, int ntheta) {
 // Pi(-khat) = conj(Pi(khat)) and M(-khat) = conj(M(khat)); with c X = c Xr +
 // i c Xi the pair of samples is S(q) = A + iB, S(-q) = A - iB, where
 // A = sum c Xr and B = sum c Xi.
+// Small angular grids pack several boxes into one block (threadIdx.y).
 template <typename Rf>
-__global__ void k_agg(int P, int ntheta, const int32_t* __restrict__ leaf_start, const C2<Rf>* __restrict__ Pi,
-                      const C2<Rf>* __restrict__ M, const C2<Rf>* __restrict__ coef, Rf mu0,
-                      C2<Rf>* __restrict__ S, int64_t sc = 0, int64_t sS = 0) {
-  const int b = blockIdx.x;
+__global__ void k_agg(int P, int ntheta, int64_t nb, const int32_t* __restrict__ leaf_start,
+                      const C2<Rf>* __restrict__ Pi, const C2<Rf>* __restrict__ M, const C2<Rf>* __restrict__ coef,
+                      Rf mu0, C2<Rf>* __restrict__ S, int64_t sc = 0, int64_t sS = 0) {
+  const int64_t b = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
+  if (b >= nb) return;
   coef += blockIdx.y * sc;
   S += blockIdx.y * sS;
   const int Ph = P / 2;
@@ -497,12 +510,14 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT, 4) k_anterp_fft(
 }
 
 // a4: translation at one level: G[d] = sum_{s in IL(d)} T[off] * S[s];
-// one block per destination box, one thread per sample, five components.
+// one destination box per threadIdx.y row of a block (several rows for small
+// angular grids), one thread per sample, five components.
 template <typename Rf>
-__global__ void k_trans(int P, const int32_t* __restrict__ il_ptr, const int32_t* __restrict__ il_idx,
+__global__ void k_trans(int P, int64_t nb, const int32_t* __restrict__ il_ptr, const int32_t* __restrict__ il_idx,
                         const int32_t* __restrict__ il_off, const C2<Rf>* __restrict__ Tt,
                         const C2<Rf>* __restrict__ S, C2<Rf>* __restrict__ G, int64_t sS = 0) {
-  int d = blockIdx.x;
+  const int64_t d = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
+  if (d >= nb) return;
   S += blockIdx.y * sS;
   G += blockIdx.y * sS;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
@@ -685,6 +700,12 @@ __global__ void k_assemble(int64_t N, int64_t E, const int32_t* __restrict__ edg
 
 static inline unsigned nblk(int64_t n, int b) { return unsigned((n + b - 1) / b); }
 
+static inline MomScale mom_scale(const Problem& pr) {
+  MomScale m;
+  for (int q = 0; q < kMom; ++q) m.s[q] = pr.mom_scale[q];
+  return m;
+}
+
 void prof_mark(Problem& pr, int stage, bool end, cudaStream_t st) {
   if (pr.prof_n >= pr.prof_cap) return;
   cudaEventRecord(pr.prof_ev[(size_t(pr.prof_n) * kStages + stage) * 2 + (end ? 1 : 0)], st);
@@ -711,7 +732,7 @@ static pie_status fft_prepare() {
   return s;
 }
 
-template <typename Rm, typename Rf, typename Rio>
+template <typename Rm, typename Rf, typename Rio, bool H16 = false>
 static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaStream_t st) {
   const int P = pr.P;
   const int L = pr.tree.L;
@@ -751,9 +772,10 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   // (RB chosen per call: a wide accumulator set costs occupancy when unused)
   auto near_launch = [&](auto rb) {
     constexpr int RB = decltype(rb)::value;
-    k_near<Rm, Rio, RB><<<dim3(near_grid, unsigned((nrhs + RB - 1) / RB)), 256, 0, sn>>>(
+    k_near<Rm, Rio, RB, H16><<<dim3(near_grid, unsigned((nrhs + RB - 1) / RB)), 256, 0, sn>>>(
         pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
-        static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot2, nrhs, sT, sT);
+        static_cast<const C2<Rm>*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, Rm(kMu0),
+        pot2, nrhs, sT, sT);
   };
   int rb = pr.tune.near_rhs_block;
   if (rb == 0) rb = nrhs == 1 ? 1 : (nrhs == 2 || sizeof(Rm) == 8) ? 2 : nrhs <= 4 ? 4 : 8;
@@ -779,8 +801,14 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   prof_mark(pr, 2, false, st);
   // far coefficients in the far precision (MIXED and FP64: the io buffer)
   const C2<Rf>* fcoef = reinterpret_cast<const C2<Rf>*>(coef);
-  k_agg<Rf><<<dim3(unsigned(pr.lev[L].nb), nr), ((P / 2 + 31) / 32) * 32, 0, st>>>(
-      P, pr.par.ntheta, pr.leaf_start, Pi, M, fcoef, Rf(kMu0), static_cast<C2<Rf>*>(pr.lev[L].S), sT, sl(L));
+  {
+    // half-grid threads per box; boxes per block so that small grids fill 128 threads
+    const int ath = P / 2 < 32 ? P / 2 : ((P / 2 + 31) / 32) * 32;
+    const int abp = ath < 64 ? 128 / ath : 1;
+    k_agg<Rf><<<dim3(nblk(pr.lev[L].nb, abp), nr), dim3(ath, abp), 0, st>>>(
+        P, pr.par.ntheta, pr.lev[L].nb, pr.leaf_start, Pi, M, fcoef, Rf(kMu0), static_cast<C2<Rf>*>(pr.lev[L].S),
+        sT, sl(L));
+  }
   prof_mark(pr, 2, true, st);
   const size_t sm = sizeof(C2<Rf>) * kComp * P;
   const bool fft8 = pr.par.ntheta == 8;
@@ -809,8 +837,9 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
       if (s != PIE_OK) return s;
       continue;
     }
-    k_trans<Rf><<<dim3(unsigned(pr.lev[l].nb), nr), tpb, 0, st>>>(
-        P, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off, static_cast<const C2<Rf>*>(pr.lev[l].trans),
+    const int tbp = tpb < 128 ? 128 / tpb : 1;  // destination boxes per block
+    k_trans<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp), 0, st>>>(
+        P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off, static_cast<const C2<Rf>*>(pr.lev[l].trans),
         static_cast<const C2<Rf>*>(pr.lev[l].S), static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
   }
   prof_mark(pr, 4, true, st);
@@ -854,7 +883,7 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
 }
 
 // Near part alone: y = Z_near x (pairs of triangles in neighbouring leaf boxes).
-template <typename Rm, typename Rio>
+template <typename Rm, typename Rio, bool H16 = false>
 static pie_status apply_near_t(Problem& pr, const void* xv, void* yv, cudaStream_t st) {
   C2<Rio>* coef = static_cast<C2<Rio>*>(pr.coef);
   C2<Rio>* pot = static_cast<C2<Rio>*>(pr.pot);
@@ -863,9 +892,9 @@ static pie_status apply_near_t(Problem& pr, const void* xv, void* yv, cudaStream
   const C2<Rm>* ncoef = split ? reinterpret_cast<const C2<Rm>*>(coef32) : reinterpret_cast<const C2<Rm>*>(coef);
   k_coef<Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const C2<Rio>*>(xv), pr.perm, pr.tri_edge,
                                                pr.tri_c, pr.tri_dcp, pr.w * pr.w * eps0(), coef, coef32);
-  k_near<Rm, Rio><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                        pr.near_idx, pr.near_off, pr.row_ptr,
-                                                        static_cast<const C2<Rm>*>(pr.mom), ncoef, Rm(kMu0), pot);
+  k_near<Rm, Rio, 1, H16><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
+      pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
+      static_cast<const C2<Rm>*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, Rm(kMu0), pot);
   k_assemble<Rio><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                    pr.inv_perm, pot, static_cast<C2<Rio>*>(yv));
   return cuda_check(cudaGetLastError(), "apply_near launch");
@@ -877,6 +906,8 @@ pie_status apply_near_one(Problem& pr, const void* x, void* y, cudaStream_t st) 
       return apply_near_t<double, double>(pr, x, y, st);
     case PIE_FP32:
       return apply_near_t<float, float>(pr, x, y, st);
+    case PIE_FP32H:
+      return apply_near_t<float, float, true>(pr, x, y, st);
     default:
       return apply_near_t<float, double>(pr, x, y, st);
   }
@@ -894,6 +925,8 @@ pie_status apply_batch(Problem& pr, const void* x, void* y, int nrhs, cudaStream
       return apply_t<float, float, float>(pr, x, y, nrhs, st);
     case PIE_MIXED:
       return apply_t<float, double, double>(pr, x, y, nrhs, st);
+    case PIE_FP32H:
+      return apply_t<float, float, float, true>(pr, x, y, nrhs, st);
   }
   set_error("unknown precision");
   return PIE_ERR_PARAM;
@@ -1125,10 +1158,16 @@ pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, v
   if (pr.io_f32()) {
     k_coef<float><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const cf*>(x), pr.perm, pr.tri_edge,
                                                    pr.tri_c, pr.tri_dcp, w2e, static_cast<cf*>(coef), nullptr);
-    k_near<float, float><<<nblk(pr.T * 32, 256), 256, 0, st>>>(pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr,
-                                                               pr.near_idx, pr.near_off, pr.row_ptr, static_cast<const cf*>(pr.mom),
-                                                               static_cast<const cf*>(coef), float(kMu0),
-                                                               static_cast<cf*>(pot));
+    if (pr.near_h16())
+      k_near<float, float, 1, true><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
+          pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr, nullptr,
+          static_cast<const __half2*>(pr.mom), mom_scale(pr), static_cast<const cf*>(coef), float(kMu0),
+          static_cast<cf*>(pot));
+    else
+      k_near<float, float><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
+          pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
+          static_cast<const cf*>(pr.mom), nullptr, mom_scale(pr), static_cast<const cf*>(coef), float(kMu0),
+          static_cast<cf*>(pot));
     k_assemble<float><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                        pr.inv_perm, static_cast<const cf*>(pot), static_cast<cf*>(y));
   } else {
@@ -1139,11 +1178,13 @@ pie_status apply_near_scratch(Problem& pr, const void* x, void* y, void* coef, v
     if (split)
       k_near<float, double><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
           pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
-          static_cast<const cf*>(pr.mom), static_cast<const cf*>(coef), float(kMu0), static_cast<cd*>(pot));
+          static_cast<const cf*>(pr.mom), nullptr, mom_scale(pr), static_cast<const cf*>(coef), float(kMu0),
+          static_cast<cd*>(pot));
     else
       k_near<double, double><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
           pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
-          static_cast<const cd*>(pr.mom), static_cast<const cd*>(coef), kMu0, static_cast<cd*>(pot));
+          static_cast<const cd*>(pr.mom), nullptr, mom_scale(pr), static_cast<const cd*>(coef), kMu0,
+          static_cast<cd*>(pot));
     k_assemble<double><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                         pr.inv_perm, static_cast<const cd*>(pot), static_cast<cd*>(y));
   }

@@ -1,5 +1,6 @@
 // Device helpers: interleaved complex arithmetic in float or double.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "problem.h"
@@ -43,6 +44,11 @@ template <typename R, typename S>
 __device__ __forceinline__ C2<R> cvt(C2<S> a) {
   return mk<R>(R(a.x), R(a.y));
 }
+// Scales of half-precision near moments (PIE_FP32H): value = stored * s[plane].
+struct MomScale {
+  float s[kMom];
+};
+
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll

@@ -108,9 +108,13 @@ struct Problem {
   uint32_t far_mask = 0xffffffffu;
   bool with_near = true;
 
+  // PIE_FP32H: moments stored as half pairs, value = stored * mom_scale[plane]
+  float mom_scale[kMom] = {1, 1, 1, 1, 1, 1, 1, 1};
+
   bool near_f32() const { return par.precision != PIE_FP64; }
-  bool far_f32() const { return par.precision == PIE_FP32; }
-  bool io_f32() const { return par.precision == PIE_FP32; }
+  bool near_h16() const { return par.precision == PIE_FP32H; }
+  bool far_f32() const { return par.precision == PIE_FP32 || par.precision == PIE_FP32H; }
+  bool io_f32() const { return far_f32(); }
 };
 
 // setup kernels (setup.cu)

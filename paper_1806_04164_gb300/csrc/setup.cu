@@ -5,6 +5,7 @@
 //  - leaf radiation tables (Pi, M) at the leaf wavenumber kappa_L;
 //  - translation operators of Eq. (5) per level and offset;
 //  - interpolation filter (degree rescale) and phases.
+#include <cstring>
 #include <cmath>
 
 #include "device.cuh"
@@ -777,12 +778,85 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   return cuda_check(cudaStreamSynchronize(st), "setup");
 }
 
+// Largest |re| and |im| of each of the eight moment planes (blockIdx.y):
+// non-negative floats order like their bit patterns, so atomicMax on those.
+__global__ void k_plane_absmax(int64_t nnz, const cf* __restrict__ mom, unsigned* __restrict__ mx) {
+  const int q = blockIdx.y;
+  float m = 0.f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x) {
+    const cf v = mom[q * nnz + e];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx + q, __float_as_uint(m));
+}
+
+// out = round-to-nearest half of (value * 2^e[plane]), plane by plane.
+__global__ void k_to_half(int64_t nnz, const cf* __restrict__ mom, MomScale mul, __half2* __restrict__ out) {
+  const int q = blockIdx.y;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x) {
+    const cf v = mom[q * nnz + e];
+    out[q * nnz + e] = __floats2half2_rn(v.x * mul.s[q], v.y * mul.s[q]);
+  }
+}
+
+// PIE_FP32H: the float moments built by setup_t become half pairs, each
+// plane scaled by the power of two that puts its largest magnitude in
+// [2^14, 2^15) (half's largest finite value is 65504); the scale's inverse is
+// kept in pr.mom_scale.  The float planes are freed.
+static pie_status moments_to_half(Problem& pr, cudaStream_t st) {
+  pie_status s = PIE_OK;
+  const int64_t nnz = pr.nnz;
+  unsigned* mx = static_cast<unsigned*>(zalloc(pr, sizeof(unsigned) * kMom, s));
+  __half2* h = static_cast<__half2*>(zalloc(pr, sizeof(__half2) * kMom * size_t(nnz), s));
+  if (s != PIE_OK) return s;
+  const unsigned grid = unsigned(std::min<int64_t>((nnz + 255) / 256, 4096));
+  cudaMemsetAsync(mx, 0, sizeof(unsigned) * kMom, st);
+  const cf* mom = static_cast<const cf*>(pr.mom);
+  k_plane_absmax<<<dim3(std::max(grid, 1u), kMom), 256, 0, st>>>(nnz, mom, mx);
+  unsigned hm[kMom];
+  if ((s = cuda_check(cudaMemcpyAsync(hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, st), "moment range")) != PIE_OK)
+    return s;
+  if ((s = cuda_check(cudaStreamSynchronize(st), "moment range")) != PIE_OK) return s;
+  MomScale mul;
+  for (int q = 0; q < kMom; ++q) {
+    float m;
+    std::memcpy(&m, &hm[q], sizeof(m));
+    int e = 0;
+    if (m > 0.f && std::isfinite(m)) std::frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+    const int sh = (m > 0.f && std::isfinite(m)) ? 15 - e : 0;
+    mul.s[q] = std::ldexp(1.0f, sh);
+    pr.mom_scale[q] = std::ldexp(1.0f, -sh);
+  }
+  k_to_half<<<dim3(std::max(grid, 1u), kMom), 256, 0, st>>>(nnz, mom, mul, h);
+  if ((s = cuda_check(cudaStreamSynchronize(st), "moments to half")) != PIE_OK) return s;
+  // release the float planes and the range buffer
+  auto release = [&](void* ptr, size_t bytes) {
+    for (size_t i = 0; i < pr.allocs.size(); ++i)
+      if (pr.allocs[i] == ptr) {
+        cudaFree(ptr);
+        pr.allocs.erase(pr.allocs.begin() + i);
+        pr.bytes -= bytes;
+        return;
+      }
+  };
+  release(pr.mom, sizeof(cf) * kMom * size_t(nnz));
+  release(mx, sizeof(unsigned) * kMom);
+  pr.mom = h;
+  return PIE_OK;
+}
+
 pie_status setup_device(Problem& pr, cudaStream_t st) {
   switch (pr.par.precision) {
     case PIE_FP64:
       return setup_t<double, double>(pr, st);
     case PIE_FP32:
       return setup_t<float, float>(pr, st);
+    case PIE_FP32H: {
+      pie_status s = setup_t<float, float>(pr, st);
+      return s == PIE_OK ? moments_to_half(pr, st) : s;
+    }
     case PIE_MIXED:
       return setup_t<float, double>(pr, st);
   }
