@@ -66,7 +66,7 @@ def test_problem_parameter_validation_on_host(libpie):
     xyz, tri = pi.icosphere(2)
     m = pg.Mesh(xyz, tri)
     bad = [dict(levels=2), dict(levels=3, tau=31), dict(levels=3, ntheta=7), dict(levels=3, kappa_a=0.0),
-           dict(levels=3, precision=3), dict(levels=3, max_nrhs=0)]
+           dict(levels=3, precision=4), dict(levels=3, precision=-1), dict(levels=3, max_nrhs=0)]
     for kw in bad:
         with pytest.raises(pg.PieError) as ei:
             pg.Problem(m, 0.01, root_side=2.0, stream=0, **kw)
