@@ -8,8 +8,13 @@ y = Z x (all stages: coefficients, near part, aggregation, interpolation,
 translations at levels 3..7, anterpolation, disaggregation, assembly) on a
 complex-normal x (seed 1234) resident in HBM.  The headline `value` is the
 MIXED form (near part complex float, far part complex double); the plain
-FP64 form is reported beside it.
+FP64 form is reported beside it.  GMRES time to 1e-6 is reported for the
+plain FP64 and MIXED solvers and for the nested solve (flexible GMRES on the
+MIXED operator, inner GMRES cycles on the complex-float PIE_FP32H operator at
+tau = 3, kappa a = 0.15, N_theta = 4).
 
+cpu_baseline times the CPU FP64 oracle MLFMA on the host cores (products on
+the 1280-triangle sphere, scaled to this workload by N x active levels);
 --impl reference times the CPU FP64 oracle (the dense Galerkin product,
 computed row by row) on a bounded sample of the same workload.
 """
@@ -28,12 +33,14 @@ WORKLOAD = dict(workload="pec_sphere_icosphere7_1M", mesh="icosphere n=7, R=1 m"
                 rwg=491520, N=819200, kR=1e-3, levels=7, leaf_m=1.0 / 32, tau=7, kappa_a=0.08, ntheta=8, P=128,
                 nrhs=1)
 METRIC = "PIE MLFMA matvecs/s (1M unk)"
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal; used only if the probe fails
 FALLBACK_HBM_GBS = 6800.0
 # DRAM read + write bytes per algorithmic flop of a stage's kernels, from one
-# ncu capture (profiles/product_kernels_icosphere6.md); valid while those
-# kernels are unchanged
-NCU_BYTES_PER_FLOP = {"translation": 78.2e6 / 1.3376e9}
+# ncu capture (profiles/); valid while those kernels are unchanged
+NCU_BYTES_PER_FLOP = {}
+# inner operator of the nested solve and its settings
+INNER = dict(tau=3, kappa_a=0.15, ntheta=4)
+NESTED = dict(inner_restart=20, inner_tol=0.1, outer_restart=80, max_outer=400, maxit=8000)
 
 
 def parse():
@@ -49,6 +56,8 @@ def parse():
     ap.add_argument("--no-multimesh", action="store_true",
                     help="skip the four-mesh, 64-right-hand-side group launch measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch settings")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the nested solve on the 3,276,800-unknown sphere (icosphere n = 8, kR = 1e-4)")
     ap.add_argument("--gmres-tol", type=float, default=1e-6)
     ap.add_argument("--mesh-level", type=int, default=7,
                     help="icosphere subdivision n (L = n levels); 7 is the timed workload, smaller for profiling")
@@ -209,6 +218,10 @@ def run_ours(args):
     mesh = pg.Mesh(xyz, tri)
     k0 = 1e-3
     stream = torch.cuda.current_stream()
+    try:  # FMA throughput of this GPU for the ALU-bound roofline
+        fp64_tf, fp32_tf = pg.measure_peaks()
+    except pg.PieError:
+        fp64_tf = fp32_tf = None
     x_host = pi.complex_normal(mesh.nt + mesh.ne, 1234)
     results = {}
     for mode, prec in (("mixed", pg.PIE_MIXED), ("fp64", pg.PIE_FP64)):
@@ -261,9 +274,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1))
-        gm = None
+        gm = nested = inner = None
         if not args.no_gmres:
             gm = gmres_run(pr, args.gmres_tol, k0, barrier, max_over_ranks)
+            if mode == "mixed":
+                nested, inner = nested_run(pg, mesh, nlev, pr, x_host, args.gmres_tol, k0, barrier,
+                                           max_over_ranks, args.no_autotune)
         # coef, near, aggregation, interpolation (L-3), translation (L-2), anterpolation (L-3),
         # sum/difference patterns, disaggregation, assembly
         launches_per = 1 + 1 + 1 + (pr.L - 3) + (pr.L - 2) + (pr.L - 3) + 1 + 1 + 1
@@ -271,7 +287,7 @@ def run_ours(args):
                              tuning=tuning,
                              e2e_ms=e2e_ms, setup_s=setup_s, launches=launches_per * args.steps,
                              bytes_io=x.numel() * x.element_size(), device_bytes=pr.device_bytes,
-                             near_pairs=pr.near_pairs, gmres=gm)
+                             near_pairs=pr.near_pairs, gmres=gm, nested=nested, inner=inner)
         del x, y, xd, yd
     # batched right-hand sides: 8 columns per pass (MIXED)
     if not args.no_batched:
@@ -296,6 +312,8 @@ def run_ours(args):
         del prb, X, Y
     if not args.no_multimesh:
         results["multimesh"] = multimesh_run(args, stream, barrier, max_over_ranks)
+    if not args.no_large and not args.no_gmres and nlev == 7:
+        results["large"] = large_nested_run(args, barrier, max_over_ranks)
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -314,11 +332,13 @@ def run_ours(args):
     else:
         achieved = amount / (per_launch_ms * 1e-3) / 1e12
         traffic = NCU_BYTES_PER_FLOP[dom] * amount if dom in NCU_BYTES_PER_FLOP else None
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal FP64",
+        peak64 = fp64_tf if fp64_tf else FP64_NOMINAL_TFLOPS
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                "frac": achieved / peak64,
+                "peak_source": ("measured: FP64 FMA probe on this GPU (pie_measure_peaks), this run" if fp64_tf
+                                else "nominal FP64"),
                 "algorithmic_flops": amount, "traffic": traffic,
-                "traffic_source": ("ncu dram bytes per flop on the 81,920-triangle sphere, scaled by flops "
-                                   "(profiles/product_kernels_icosphere6.md)") if traffic else None}
+                "traffic_source": "ncu dram bytes per flop, scaled by flops (profiles/)" if traffic else None}
     stage_share = {k: round(v / sum(main["stage_ms"].values()), 4) for k, v in main["stage_ms"].items()}
     fp = results["fp64"]
     line = {
@@ -337,29 +357,34 @@ def run_ours(args):
         "config": dict(WORKLOAD if nlev == 7 else dict(workload=f"pec_sphere_icosphere{nlev}", N=pr.N, levels=pr.L),
                        precision="mixed", parallelism=f"replicas{world}",
                        l2="working set > L2 (near moments %.1f GB), no flush" % (main["near_pairs"] * 64 / 1e9)),
-        "tuning": main["tuning"],
         "e2e": {"value": world * K / (main["e2e_ms"] * 1e-3), "unit": "matvecs/s",
                 "h2d_bytes_per_step": main["bytes_io"], "d2h_bytes_per_step": main["bytes_io"]},
         "gpu_launches": main["launches"],
         "roofline": roof,
-        "stage_ms_per_step": {k: v / K for k, v in main["stage_ms"].items()},
+        "clocks": main["clocks"],
+        "tuning": main["tuning"],
+        "stage_ms_per_step": {k: round(v / K, 4) for k, v in main["stage_ms"].items()},
         "stage_share": stage_share,
-        "fp64": {"value": world * K / (fp["ms"] * 1e-3), "ms_per_step": fp["ms"] / K,
-                 "stage_ms_per_step": {k: v / K for k, v in fp["stage_ms"].items()},
-                 "e2e_value": world * K / (fp["e2e_ms"] * 1e-3), "setup_s": fp["setup_s"], "tuning": fp["tuning"],
-                 "gmres": fp["gmres"]},
-        "gmres": main["gmres"],
+        "setup_s": main["setup_s"],
+        "device_bytes": main["device_bytes"],
+        "multimesh": results.get("multimesh"),
         "batched8": ({"value": world * K * results["batched"]["nrhs"] / (results["batched"]["ms"] * 1e-3),
                       "unit": "matvecs/s", "nrhs": results["batched"]["nrhs"], "precision": "mixed",
                       "ms_per_batch": results["batched"]["ms"] / K, "tuning": results["batched"]["tuning"]}
                      if "batched" in results else None),
-        "multimesh": results.get("multimesh"),
-        "setup_s": main["setup_s"],
-        "device_bytes": main["device_bytes"],
-        "clocks": main["clocks"],
     }
     if not args.no_cpu_baseline and nlev == 7:
         line["cpu_baseline"] = cpu_baseline(args.cpu_rows)
+    # the summaries the comparison rests on come last (the tail of the line)
+    line["inner_fp32h"] = main["inner"]
+    line["fp64"] = {"value": world * K / (fp["ms"] * 1e-3), "ms_per_step": fp["ms"] / K,
+                    "e2e_value": world * K / (fp["e2e_ms"] * 1e-3),
+                    "stage_ms_per_step": {k: round(v / K, 4) for k, v in fp["stage_ms"].items()}}
+    line["peaks_tflops"] = {"fp64": fp64_tf, "fp32": fp32_tf}
+    line["gmres_fp64"] = fp["gmres"]
+    line["gmres"] = main["gmres"]
+    line["gmres_nested"] = main["nested"]
+    line["large_nested"] = results.get("large")
     print(json.dumps(line))
 
 
@@ -385,15 +410,7 @@ def multimesh_run(args, stream, barrier, max_over_ranks):
     import pie_inputs as pi
     k0, nrhs = 1e-2, 64
     steps = min(args.steps, 20)  # one launch is 4 x 64 products (~0.15 s)
-    th = (np.arange(4) + 0.5) * np.pi / 4
-    ph = np.arange(8) * 2 * np.pi / 8
-    waves = []
-    for t in th:
-        for p in ph:
-            kh = -np.array([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)])
-            e_th = np.array([np.cos(t) * np.cos(p), np.cos(t) * np.sin(p), -np.sin(t)])
-            e_ph = np.array([-np.sin(p), np.cos(p), 0.0])
-            waves += [(kh, e_th), (kh, e_ph)]
+    waves = pi.planewave_set()
     members, info = [], []
     t0 = time.time()
     for name, gen, side, (lmin, lmax) in MULTIMESH:
@@ -447,6 +464,42 @@ def multimesh_run(args, stream, barrier, max_over_ranks):
     return out
 
 
+def large_nested_run(args, barrier, max_over_ranks):
+    """The large sphere (icosphere n = 8: 1,310,720 triangles, N = 3,276,800,
+    kR = 1e-4, 8 levels): nested solve to 1e-6 (MIXED outer operator,
+    PIE_FP32H inner operator at INNER, settings NESTED) for the x-polarised
+    plane wave along -z, and the E-plane RCS of the solution against the
+    Rayleigh limit.  Set-up untimed and reported; plain GMRES on this sphere
+    runs under --workload large."""
+    import torch
+
+    import paper_1806_04164_gb300 as pg
+    import pie_inputs as pi
+    k0, n, L = 1e-4, 8, 8
+    mesh = pg.Mesh(*pi.icosphere(n))
+    t0 = time.time()
+    po = pg.Problem(mesh, k0, L, root_side=2.0, precision=pg.PIE_MIXED)
+    pin = pg.Problem(mesh, k0, L, root_side=2.0, precision=pg.PIE_FP32H, **INNER)
+    setup_s = time.time() - t0
+    if not args.no_autotune:
+        po.autotune(nrhs=1, reps=3)
+        pin.autotune(nrhs=1, reps=3)
+    b = po.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
+    torch.cuda.synchronize()
+    barrier()
+    x, st = po.solve_nested(b, pin, tol=args.gmres_tol, **NESTED)
+    barrier()
+    out = {"workload": "pec_sphere_icosphere8_3M", "N": po.N, "kR": k0, "levels": L, "tol": args.gmres_tol,
+           "seconds": max_over_ranks(st["seconds"]), "converged": st["converged"], "rel_residual": st["rel_residual"],
+           "inner_iterations": st["inner_iterations"], "outer_products": st["outer_products"],
+           "inner_product_seconds": st["inner_product_seconds"], "outer_product_seconds": st["outer_product_seconds"],
+           "rcs_max_db_err_vs_rayleigh": rcs_err_db(po, x, k0), "setup_s_both": setup_s,
+           "device_bytes": po.device_bytes + pin.device_bytes}
+    del po, pin, x, b
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_large(args):
     """Icosphere n = 8 (1,310,720 triangles, 1,966,080 RWG, N = 3,276,800),
     kR = 1e-4; level count by the autotuner among 8 and 9.  Per precision
@@ -494,6 +547,16 @@ def run_large(args):
             res[f"nrhs{cols}"] = {"ms_per_pass": ms, "matvecs_per_s": cols / (ms * 1e-3)}
         del X, Y
         res["gmres"] = gmres_run(pr, args.gmres_tol, k0, noop, lambda v: v)
+        if mode == "mixed":
+            pin = pg.Problem(mesh, k0, L, root_side=2.0, precision=pg.PIE_FP32H, **INNER)
+            pin.autotune(nrhs=1, reps=3)
+            b = pr.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
+            xs, st = pr.solve_nested(b, pin, tol=args.gmres_tol, **NESTED)
+            res["gmres_nested"] = {"seconds": st["seconds"], "converged": st["converged"],
+                                   "inner_iterations": st["inner_iterations"],
+                                   "outer_products": st["outer_products"],
+                                   "rcs_max_db_err_vs_rayleigh": rcs_err_db(pr, xs, k0)}
+            del pin
         out[mode] = res
         del pr
         torch.cuda.empty_cache()
@@ -527,8 +590,74 @@ def gmres_run(pr, tol, k0, barrier, max_over_ranks):
     return {"tol": tol, "iterations": st["iterations"], "seconds": max_over_ranks(st["seconds"]),
             "product_seconds": st["product_seconds"], "reorthogonalizations": st["reorthogonalizations"],
             "rel_residual": st["rel_residual"], "converged": st["converged"], "restart": 300,
-            "rcs_max_db_err_vs_rayleigh": float(np.max(np.abs(10 * np.log10(s[mask] / sm[mask])))),
-            "rcs_db": [float(v) for v in 10 * np.log10(s[::30])]}
+            "rcs_max_db_err_vs_rayleigh": float(np.max(np.abs(10 * np.log10(s[mask] / sm[mask]))))}
+
+
+def rcs_err_db(pr, x, k0):
+    """Largest |RCS - Rayleigh| in dB over the E-plane directions within 20 dB
+    of the Rayleigh maximum (the null near 60 degrees is left out)."""
+    import numpy as np
+
+    import pie_inputs as pi
+    rh = pi.bistatic_directions(181)
+    E = pr.farfield(x, rh).cpu().numpy()
+    s = 4 * np.pi * np.sum(np.abs(E) ** 2, axis=1)
+    sm = rayleigh_eplane(k0, 1.0, -rh[:, 2])
+    mask = sm > 1e-2 * sm.max()
+    return float(np.max(np.abs(10 * np.log10(s[mask] / sm[mask]))))
+
+
+def nested_run(pg, mesh, nlev, po, x_host, tol, k0, barrier, max_over_ranks, no_autotune):
+    """Nested solve to ||b - Z x|| <= tol ||b|| (Z: the MIXED operator po) for
+    the plane wave along -z, x-polarised: flexible GMRES on po, each outer
+    step preconditioned by one GMRES cycle on the complex-float PIE_FP32H
+    operator at INNER (set-up and autotuning untimed).  Also the inner
+    operator's product time and the HBM roofline of its near kernel."""
+    import torch
+    stream = torch.cuda.current_stream()
+    pin = pg.Problem(mesh, k0, nlev, root_side=2.0, precision=pg.PIE_FP32H, **INNER)
+    if not no_autotune:
+        pin.autotune(nrhs=1, reps=5)
+    x = torch.from_numpy(x_host).to(torch.complex64).cuda()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        pin.apply(x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        pin.apply(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    pin.profile_begin(reps)
+    for _ in range(reps):
+        pin.apply(x, y)
+    stage_ms, na = pin.profile_end()
+    near_ms = stage_ms["near"] / max(1, na)
+    near_bytes = pin.near_pairs * 32 + pin.T * 6 * 8 * 2   # half moments once, float coefficients in, potentials out
+    hbm, hbm_src = peaks()
+    inner = {"point": dict(INNER), "precision": "fp32h", "ms_per_product": ms, "matvecs_per_s": 1e3 / ms,
+             "stage_ms": {k: round(v / max(1, na), 4) for k, v in stage_ms.items()},
+             "near_roofline": {"bound": "hbm", "achieved": near_bytes / (near_ms * 1e-3) / 1e9, "peak": hbm,
+                               "unit": "GB/s", "frac": near_bytes / (near_ms * 1e-3) / 1e9 / hbm,
+                               "peak_source": hbm_src, "algorithmic_bytes": near_bytes},
+             "device_bytes": pin.device_bytes}
+    b = po.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
+    torch.cuda.synchronize()
+    barrier()
+    xs, st = po.solve_nested(b, pin, tol=tol, **NESTED)
+    barrier()
+    nested = {"tol": tol, "seconds": max_over_ranks(st["seconds"]), "converged": st["converged"],
+              "rel_residual": st["rel_residual"], "inner_iterations": st["inner_iterations"],
+              "outer_iterations": st["outer_iterations"], "outer_products": st["outer_products"],
+              "inner_product_seconds": st["inner_product_seconds"],
+              "outer_product_seconds": st["outer_product_seconds"], "settings": dict(NESTED),
+              "rcs_max_db_err_vs_rayleigh": rcs_err_db(po, xs, k0)}
+    del pin, x, y
+    torch.cuda.empty_cache()
+    return nested, inner
 
 
 CPU_SNIPPET = r"""
@@ -538,6 +667,23 @@ import numpy as np
 import pie_inputs as pi
 from oracle.dense import rows
 from oracle.mesh import build_topology
+from oracle.mlfma import MLFMA
+out = {}
+# oracle MLFMA on the 1280-triangle sphere (N = 3200), 3 levels
+xyz, tri = pi.icosphere(3)
+t0 = time.time()
+M = MLFMA(xyz, tri, 1e-3, 3, side=2.0)
+out["mlfma_setup_s"] = time.time() - t0
+x = pi.complex_normal(M.top.N, 1234)
+M.apply(x)
+ts = []
+for _ in range(3):
+    t0 = time.time()
+    M.apply(x)
+    ts.append(time.time() - t0)
+out["mlfma_mvm_s"] = float(np.median(ts))
+out["mlfma_N"] = int(M.top.N)
+# dense Galerkin rows of the 819,200-unknown sphere itself
 xyz, tri = pi.icosphere(7)
 top = build_topology(xyz, tri)
 x = pi.complex_normal(top.N, 1234)
@@ -545,23 +691,53 @@ which = [0, top.E // 2, top.E + 5, top.N - 1][:NROWS]
 rows(top, 1e-3, which[:1], x)          # warm-up (caches, page-in)
 t0 = time.time()
 rows(top, 1e-3, which, x)
-dt = time.time() - t0
-print(json.dumps({"rows": len(which), "seconds": dt, "N": top.N}))
+out["rows"] = len(which)
+out["rows_s"] = time.time() - t0
+out["N"] = int(top.N)
+print(json.dumps(out))
 """
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform_processor()
+
+
+def platform_processor():
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(nrows):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    """The CPU FP64 oracle on all host cores (numpy with its BLAS on every
+    core): MLFMA products on the 1280-triangle sphere (N = 3200, one
+    translation level), scaled to the 819,200-unknown, 5-translation-level
+    workload by N x active levels (the O(N L) cost of the method, Section 4);
+    beside it, exact dense Galerkin rows of the workload itself."""
+    ncpu = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(ncpu), OPENBLAS_NUM_THREADS=str(ncpu), MKL_NUM_THREADS=str(ncpu))
     code = CPU_SNIPPET.replace("ROOTDIR", repr(ROOT)).replace("NROWS", str(int(nrows)))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
         return {"error": out.stderr.strip().splitlines()[-1] if out.stderr else "failed"}
     d = json.loads(out.stdout.strip().splitlines()[-1])
-    value = d["rows"] / d["seconds"] / d["N"]
-    return {"value": value, "unit": "matvecs/s", "cores": 1, "kind": "oracle",
-            "sample": f"{d['rows']} rows of the dense FP64 Galerkin product y = Z x on the same "
-                      f"819,200-unknown sphere ({d['seconds']:.1f} s, single thread); "
-                      f"matvecs/s = rows/s / N"}
+    scale = (WORKLOAD["N"] * (WORKLOAD["levels"] - 2)) / (d["mlfma_N"] * 1)
+    value = 1.0 / (d["mlfma_mvm_s"] * scale)
+    return {"value": value, "unit": "matvecs/s", "cores": ncpu, "cpu_model": cpu_model(), "kind": "oracle MLFMA",
+            "sample": (f"oracle MLFMA (numpy FP64) products on the 1280-triangle sphere (N = {d['mlfma_N']}, L = 3, "
+                       f"one translation level): {d['mlfma_mvm_s']:.3f} s per product after a "
+                       f"{d['mlfma_setup_s']:.1f} s set-up; matvecs/s at N = 819,200, 5 translation levels = "
+                       f"1 / (t x {scale:.0f}), the N x active-levels ratio"),
+            "mlfma_mvm_s_1280": d["mlfma_mvm_s"], "mlfma_setup_s_1280": d["mlfma_setup_s"],
+            "dense_rows": {"value": d["rows"] / d["rows_s"] / d["N"], "unit": "matvecs/s",
+                           "sample": f"{d['rows']} rows of the dense FP64 Galerkin product of this workload, "
+                                     f"{d['rows_s']:.1f} s; matvecs/s = rows/s / N"}}
 
 
 def run_reference(args):

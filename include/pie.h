@@ -207,12 +207,14 @@ pie_status pie_apply_levels(pie_problem* pr, const void* x, void* y, uint32_t le
  * fixed 24 MiB device array inside the library, which every GPU that loads
  * the library holds until the process exits; meshes above 131072 triangles
  * (complex double) or 262144 (complex float) are rejected with
- * PIE_ERR_PARAM.  The first call on a device looks the array's device
- * address up (cudaGetSymbolAddress) and must come before any stream capture
- * on that device.  All calls share the array and every call overwrites the
- * parts it reads, so nothing carries over between calls; calls that overlap
- * on the GPU (different streams, or different problems at once) race on
- * it.  Errors: PIE_ERR_PARAM, PIE_ERR_CUDA. */
+ * PIE_ERR_PARAM.  The array's device address is looked up
+ * (cudaGetSymbolAddress) by pie_problem_create, on the device current there,
+ * and kept in the problem; so the entry point itself does no set-up and may
+ * be called inside a stream capture, and it returns PIE_ERR_PARAM when the
+ * current device is not the problem's.  All calls share the array and every
+ * call overwrites the parts it reads, so nothing carries over between calls;
+ * calls that overlap on the GPU (different streams, or different problems
+ * at once) race on it.  Errors: PIE_ERR_PARAM, PIE_ERR_CUDA. */
 pie_status pie_apply_near_noalloc(pie_problem* pr, const void* x, void* y, int dtype, void* stream);
 
 /* Per-stage timing of products (CUDA events recorded on the apply stream
@@ -333,6 +335,9 @@ pie_status pie_solve_guess(pie_problem* pr, const void* b, void* x, int nrhs, do
  *   outer_restart: outer steps per restart (1..200); 0 = iterative
  *     refinement (x += D z for the preconditioned scaled residual);
  *   max_outer: bound on products with the outer operator per column.
+ * An outer cycle ends when its residual estimate reaches tol (or after
+ * outer_restart steps); the FP64 true residual then decides whether the
+ * column has converged or another cycle starts.
  * Synchronises the stream.  Returns PIE_OK when every column converged, else
  * PIE_ERR_NOCONV of the first column that did not; PIE_ERR_PARAM (mismatched
  * problems, PIE_FP32 outer problem, parameters out of range), PIE_ERR_OOM,
@@ -441,6 +446,15 @@ pie_status pie_problem_autotune(pie_problem* pr, int nrhs, int reps, pie_tuning*
  * Errors: PIE_ERR_PARAM, PIE_ERR_LEAF (no admissible L), the set-up errors. */
 pie_status pie_tune_levels(const pie_mesh* m, double k0, const pie_params* base, int lmin, int lmax, int nrhs,
                            void* stream, int* best_levels, double* ms_per_level);
+
+/* Arithmetic peaks of the current device for the roofline of the ALU-bound
+ * kernels (the paper has no counterpart: a measurement aid).  Times fused
+ * multiply-add chains (eight independent chains per thread, 4 blocks of 256
+ * threads per SM) in real FP64 and FP32 with CUDA events on the
+ * stream, best of three launches after ten untimed ones, about 0.5 s in all;
+ * writes TFLOP/s (2 flop per FMA) to the host doubles.  Synchronises the
+ * stream.  Errors: PIE_ERR_PARAM (NULL output), PIE_ERR_CUDA. */
+pie_status pie_measure_peaks(double* fp64_tflops, double* fp32_tflops, void* stream);
 
 /* Multi-mesh batch: several problems (meshes of uneven size, any
  * wavenumbers and precisions) applied to nrhs right-hand sides each in ONE

@@ -77,7 +77,7 @@ EXPORTS = ["pie_last_error", "pie_params_default", "pie_mesh_create", "pie_mesh_
            "pie_nearfield", "pie_problem_get_tuning", "pie_problem_set_tuning", "pie_problem_autotune",
            "pie_tune_levels", "pie_group_create", "pie_group_apply", "pie_group_info", "pie_group_destroy",
            "pie_apply_levels", "pie_problem_quadrature", "pie_rhs_potentials", "pie_solve_guess",
-           "pie_solve_nested"]
+           "pie_solve_nested", "pie_measure_peaks"]
 STAGES = ["coef", "near", "aggregation", "interpolation", "translation", "anterpolation", "disaggregation",
           "assembly"]
 
@@ -124,6 +124,7 @@ def lib():
         L.pie_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
         L.pie_solve_guess.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
         L.pie_apply_levels.argtypes = [vp, vp, vp, ctypes.c_uint32, i32, i32, vp]
+        L.pie_measure_peaks.argtypes = [PD, PD, vp]
         L.pie_solve_nested.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(NestedParams),
                                        ctypes.POINTER(NestedStats), vp]
         PT = ctypes.POINTER(Tuning)
@@ -440,7 +441,7 @@ class Problem:
                       product_seconds=s.product_seconds) for s in st[:nrhs]]
         return (x, stats[0]) if b.dim() == 1 else (x, stats)
 
-    def solve_nested(self, b, inner, tol=1e-6, maxit=20000, inner_restart=60, inner_tol=1e-2, outer_restart=20,
+    def solve_nested(self, b, inner, tol=1e-6, maxit=20000, inner_restart=20, inner_tol=0.1, outer_restart=40,
                      max_outer=400, stream=None):
         """Nested mixed-precision solve (pie_solve_nested): flexible GMRES on
         this problem's operator, each outer step preconditioned by one GMRES
@@ -502,6 +503,14 @@ def tune_levels(mesh, k0, lmin, lmax, nrhs=1, root_side=0.0, tau=DEFAULT_TAU, ka
     _check(lib().pie_tune_levels(mesh.handle, float(k0), ctypes.byref(p), lmin, lmax, nrhs, _stream(stream),
                                  ctypes.byref(best), _ptr(ms, ctypes.c_double)))
     return best.value, {lmin + i: float(v) for i, v in enumerate(ms) if v > 0}
+
+
+def measure_peaks(stream=None):
+    """FP64 and FP32 fused multiply-add throughput of the current device in
+    TFLOP/s (pie_measure_peaks)."""
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pie_measure_peaks(ctypes.byref(f64), ctypes.byref(f32), _stream(stream)))
+    return f64.value, f32.value
 
 
 class Group:

@@ -12,6 +12,17 @@
 namespace pie {
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
+
+pie_status check_device(const Problem& pr, const char* who) {
+  int dev = -1;
+  pie_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (s == PIE_OK && dev != pr.device) {
+    set_error(std::string(who) + ": the current device (" + std::to_string(dev) +
+              ") is not the one the problem was built on (" + std::to_string(pr.device) + ")");
+    s = PIE_ERR_PARAM;
+  }
+  return s;
+}
 }  // namespace pie
 
 using namespace pie;
@@ -132,7 +143,9 @@ pie_status pie_problem_create(const pie_mesh* m, double k0, const pie_params* pa
       s = PIE_ERR_PARAM;
     }
   }
+  if (s == PIE_OK) s = cuda_check(cudaGetDevice(&pr.device), "cudaGetDevice");
   if (s == PIE_OK) s = setup_device(pr, static_cast<cudaStream_t>(stream));
+  if (s == PIE_OK) s = noalloc_bind(pr);
   if (s != PIE_OK) {
     free_problem(pr);
     delete h;
@@ -223,6 +236,7 @@ static pie_status apply_api(pie_problem* h, const void* x, void* y, int nrhs, in
     set_error("pie_apply: dtype does not match the problem precision");
     return PIE_ERR_PARAM;
   }
+  if (pie_status sd = check_device(pr, "pie_apply")) return sd;
   size_t es = pr.io_f32() ? sizeof(cf) : sizeof(cd);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (near) {
@@ -253,6 +267,7 @@ pie_status pie_apply_levels(pie_problem* h, const void* x, void* y, uint32_t lev
     set_error("pie_apply_levels: dtype does not match the problem precision");
     return PIE_ERR_PARAM;
   }
+  if (pie_status sd = check_device(pr, "pie_apply_levels")) return sd;
   pr.far_mask = level_mask;
   pr.with_near = near == 1;
   pie_status s = apply_batch(pr, x, y, 1, static_cast<cudaStream_t>(stream));
@@ -275,6 +290,7 @@ pie_status pie_apply_t(pie_problem* h, const void* x, void* y, int nrhs, int dty
     set_error("pie_apply_t: dtype does not match the problem precision");
     return PIE_ERR_PARAM;
   }
+  if (pie_status sd = check_device(pr, "pie_apply_t")) return sd;
   size_t es = pr.io_f32() ? sizeof(cf) : sizeof(cd);
   for (int j = 0; j < nrhs; ++j) {
     pie_status s = apply_t_one(pr, static_cast<const char*>(x) + es * size_t(pr.N) * j,
@@ -438,6 +454,7 @@ static pie_status solve_cols(pie_problem* h, const void* b, void* x, int nrhs, d
   // one GMRES per column; a column that does not converge does not stop the
   // others, a failure of the device or the arithmetic does
   Problem& pr = h->p;
+  if (pie_status sd = check_device(pr, "pie_solve")) return sd;
   const size_t col = sizeof(cd) * size_t(pr.N);
   pie_status worst = PIE_OK;
   std::string msg;
@@ -486,6 +503,11 @@ pie_status pie_solve_nested(pie_problem* ho, pie_problem* hi, const void* b, voi
     set_error("pie_solve_nested: inner and outer problems differ in mesh or k0");
     return PIE_ERR_PARAM;
   }
+  if (pi.device != po.device) {
+    set_error("pie_solve_nested: inner and outer problems are on different devices");
+    return PIE_ERR_PARAM;
+  }
+  if (pie_status sd = check_device(po, "pie_solve_nested")) return sd;
   const size_t col = sizeof(cd) * size_t(po.N);
   pie_status worst = PIE_OK;
   std::string msg;

@@ -143,6 +143,102 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
   }
 }
 
+// a1, one right-hand side, float near part: one block per leaf box (grid
+// stride over boxes).  Every test triangle of a box runs over the same
+// source list (the concatenated source ranges of its near boxes), so the
+// block stages those sources' coefficients in shared memory once, plane by
+// plane ([6][len]), and its warps take the box's test triangles in turn,
+// lanes over the row as in k_near (lane j, j + 32, ...; the same order of
+// operations, so the same result to the last bit).  Rows longer than
+// kNearStage read the coefficients from global memory instead.
+constexpr int kNearStage = 512;
+template <typename Rio, bool H16>
+__global__ void __launch_bounds__(256) k_near_box(int64_t nleaf, int64_t nnz, const int32_t* __restrict__ leaf_start,
+                                                  const int32_t* __restrict__ near_ptr,
+                                                  const int32_t* __restrict__ near_idx,
+                                                  const int32_t* __restrict__ near_off,
+                                                  const int64_t* __restrict__ row_ptr, const cf* __restrict__ mom,
+                                                  const __half2* __restrict__ momh, MomScale msc,
+                                                  const cf* __restrict__ coef, float mu0, C2<Rio>* __restrict__ pot,
+                                                  int64_t sc = 0, int64_t sp = 0) {
+  __shared__ cf cs[6][kNearStage];
+  coef += blockIdx.y * sc;  // right-hand side blockIdx.y
+  pot += blockIdx.y * sp;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int64_t b = blockIdx.x; b < nleaf; b += gridDim.x) {
+    const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
+    const int t0 = leaf_start[b], t1 = leaf_start[b + 1];
+    const int len = int(row_ptr[t0 + 1] - row_ptr[t0]);
+    const bool staged = len <= kNearStage;
+    __syncthreads();  // the previous box's readers are done with cs
+    if (staged) {
+      for (int j = threadIdx.x; j < len; j += blockDim.x) {
+        int qi = q0;
+        while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
+        const cf* c = coef + 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cs[k][j] = c[k];
+      }
+    }
+    __syncthreads();
+    for (int t = t0 + warp; t < t1; t += nwarp) {
+      const int64_t e0 = row_ptr[t];
+      cf acc[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) acc[i] = mk<float>(0, 0);
+      int qi = q0;
+      for (int j = lane; j < len; j += 32) {
+        const int64_t ee = e0 + j;
+        cf m0, mt0, mt1, mt2, ms0, ms1, ms2, mts;
+        if constexpr (H16) {
+          auto ld = [&](int q) {
+            const float2 v = __half22float2(momh[q * nnz + ee]);
+            return mk<float>(v.x * msc.s[q], v.y * msc.s[q]);
+          };
+          m0 = ld(0), mt0 = ld(1), mt1 = ld(2), mt2 = ld(3), ms0 = ld(4), ms1 = ld(5), ms2 = ld(6), mts = ld(7);
+        } else {
+          m0 = mom[ee];
+          mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
+          ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
+          mts = mom[7 * nnz + ee];
+        }
+        cf a, b0, b1, b2, sg, dd;
+        if (staged) {
+          a = cs[0][j], b0 = cs[1][j], b1 = cs[2][j], b2 = cs[3][j], sg = cs[4][j], dd = cs[5][j];
+        } else {
+          while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
+          const cf* c = coef + 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
+          a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
+        }
+        cfma(acc[0], a, mts);
+        cfma(acc[0], b0, mt0);
+        cfma(acc[0], b1, mt1);
+        cfma(acc[0], b2, mt2);
+        cfma(acc[1], a, ms0);
+        cfma(acc[1], b0, m0);
+        cfma(acc[2], a, ms1);
+        cfma(acc[2], b1, m0);
+        cfma(acc[3], a, ms2);
+        cfma(acc[3], b2, m0);
+        cfma(acc[4], sg, m0);
+        cfma(acc[5], dd, m0);
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        acc[i].x = warp_sum(acc[i].x);
+        acc[i].y = warp_sum(acc[i].y);
+      }
+      if (lane == 0) {
+        C2<Rio>* o = pot + 6 * int64_t(t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = mk<Rio>(Rio(mu0 * acc[i].x), Rio(mu0 * acc[i].y));
+        o[4] = cvt<Rio>(acc[4]);
+        o[5] = cvt<Rio>(acc[5]);
+      }
+    }
+  }
+}
+
 // Antipode of half-grid sample q (theta rows 0..ntheta/2-1): -khat_q is
 // the sample (ntheta-1-i, j+ntheta mod 2 ntheta).
 __device__ __forceinline__ int antipode(int q, int ntheta) {
@@ -781,7 +877,16 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   if (rb == 0) rb = nrhs == 1 ? 1 : (nrhs == 2 || sizeof(Rm) == 8) ? 2 : nrhs <= 4 ? 4 : 8;
   if (!with_near)
     pot2 = nullptr;
-  else if (rb == 1)
+  else if (rb == 1 && sizeof(Rm) == 4) {
+    // one right-hand side per pass over the moments, float near part: a block per leaf box
+    unsigned grid = unsigned(pr.nleaf);
+    if (overlap && pr.tune.near_ctas_per_sm > 0)
+      grid = std::min<unsigned>(grid, unsigned(pr.nsm * pr.tune.near_ctas_per_sm));
+    k_near_box<Rio, H16><<<dim3(grid, nr), 256, 0, sn>>>(
+        pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
+        static_cast<const cf*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr),
+        reinterpret_cast<const cf*>(ncoef), float(kMu0), pot2, sT, sT);
+  } else if (rb == 1)
     near_launch(std::integral_constant<int, 1>());
   else if (rb == 2)
     near_launch(std::integral_constant<int, 2>());
@@ -892,9 +997,15 @@ static pie_status apply_near_t(Problem& pr, const void* xv, void* yv, cudaStream
   const C2<Rm>* ncoef = split ? reinterpret_cast<const C2<Rm>*>(coef32) : reinterpret_cast<const C2<Rm>*>(coef);
   k_coef<Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const C2<Rio>*>(xv), pr.perm, pr.tri_edge,
                                                pr.tri_c, pr.tri_dcp, pr.w * pr.w * eps0(), coef, coef32);
-  k_near<Rm, Rio, 1, H16><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
-      pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
-      static_cast<const C2<Rm>*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, Rm(kMu0), pot);
+  if constexpr (sizeof(Rm) == 4)
+    k_near_box<Rio, H16><<<unsigned(pr.nleaf), 256, 0, st>>>(
+        pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
+        static_cast<const cf*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, float(kMu0), pot);
+  else
+    k_near<Rm, Rio, 1, H16><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
+        pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
+        static_cast<const C2<Rm>*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, Rm(kMu0),
+        pot);
   k_assemble<Rio><<<nblk(pr.N, 256), 256, 0, st>>>(pr.N, pr.E, pr.edge_tt, pr.edge_k, pr.tri_c, pr.tri_dcp,
                                                    pr.inv_perm, pot, static_cast<C2<Rio>*>(yv));
   return cuda_check(cudaGetLastError(), "apply_near launch");

@@ -8,8 +8,6 @@
 // takes its per-triangle scratch (local coefficients and potentials) from the
 // file-scope device array below instead of the problem's own buffers, and it
 // calls no allocating routine.
-#include <mutex>
-
 #include "handles.h"
 
 namespace pie {
@@ -20,29 +18,15 @@ namespace pie {
 constexpr size_t kNoAllocScratchBytes = size_t(24) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device.  In host
-// code the array's name is only a host-side stand-in, never a device address.
-constexpr int kMaxDevices = 64;
-static void* g_scratch_addr[kMaxDevices] = {nullptr};
-static std::mutex g_scratch_mu;
-
-static pie_status scratch_address(void** out) {
-  int dev = 0;
-  pie_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
-  if (s != PIE_OK) return s;
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("pie_apply_near_noalloc: device ordinal out of range");
-    return PIE_ERR_PARAM;
-  }
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    s = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
-    if (s != PIE_OK) return s;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
-  return PIE_OK;
+// Device address of g_noalloc_scratch on the problem's device, looked up
+// when the problem is created (pie_problem_create runs outside any stream
+// capture, with that device current) and kept in the problem.  In host code
+// the array's name is only a host-side stand-in, never a device address.
+pie_status noalloc_bind(Problem& pr) {
+  void* p = nullptr;
+  pie_status s = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+  if (s == PIE_OK) pr.noalloc_scratch = p;
+  return s;
 }
 
 }  // namespace pie
@@ -69,10 +53,9 @@ extern "C" pie_status pie_apply_near_noalloc(pie_problem* h, const void* x, void
               " triangles; the limit is " + std::to_string(kNoAllocScratchBytes / (12 * es)) + ")");
     return PIE_ERR_PARAM;
   }
-  void* base = nullptr;
-  pie_status s = scratch_address(&base);
+  pie_status s = check_device(pr, "pie_apply_near_noalloc");
   if (s != PIE_OK) return s;
-  char* coef = static_cast<char*>(base);
+  char* coef = static_cast<char*>(pr.noalloc_scratch);
   char* pot = coef + need / 2;
   return apply_near_scratch(pr, x, y, coef, pot, static_cast<cudaStream_t>(stream));
 }

@@ -102,6 +102,8 @@ struct Problem {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int nsm = 0;                   // SMs of the device
+  int device = 0;                // the device the problem was built on (current at pie_problem_create)
+  void* noalloc_scratch = nullptr;  // device address of the fixed scratch of pie_apply_near_noalloc
   pie_tuning tune{1, 2, 1, 0};
   // parts of the product that run (pie_apply_levels): translations at the
   // levels whose bit is set, and the near part
@@ -150,6 +152,10 @@ pie_status solve_nested(Problem& outer, Problem& inner, const void* b, void* x, 
                         pie_nested_stats* stats, cudaStream_t st);
 
 pie_status cuda_check(cudaError_t e, const char* what);
+// looks up the fixed scratch of pie_apply_near_noalloc on the current device (noalloc.cu)
+pie_status noalloc_bind(Problem& pr);
+// PIE_ERR_PARAM unless the current device is the one the problem was built on
+pie_status check_device(const Problem& pr, const char* who);
 void* dalloc(Problem& pr, size_t bytes);
 
 }  // namespace pie

@@ -252,6 +252,39 @@ __global__ void k_combine(int64_t N, int nv, const C2<B>* __restrict__ V, int64_
   out[n] = mk<double>(r, i);
 }
 
+// partial[block] = sum over the block's entries of |(sum_v c[v] V[v][n]) / d[n]|^2:
+// pass 1 of ||D^-1 V c||^2 (finished by k_mdot_finish).  Block size kRedThreads.
+template <typename B>
+__global__ void __launch_bounds__(kRedThreads) k_resnorm(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv,
+                                                         const cd* __restrict__ c, const double* __restrict__ d,
+                                                         cd* __restrict__ partial) {
+  extern __shared__ cd cc[];
+  __shared__ double sn[kRedThreads / 32];
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) cc[v] = c[v];
+  __syncthreads();
+  const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double nrm = 0;
+  if (n < N) {
+    double r = 0, i = 0;
+    for (int v = 0; v < nv; ++v) {
+      const C2<B> a = V[v * ldv + n];
+      r += cc[v].x * double(a.x) - cc[v].y * double(a.y);
+      i += cc[v].x * double(a.y) + cc[v].y * double(a.x);
+    }
+    r /= d[n];
+    i /= d[n];
+    nrm = r * r + i * i;
+  }
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) sn[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < kRedThreads / 32; ++k) t += sn[k];
+    partial[blockIdx.x] = mk<double>(t, 0.0);
+  }
+}
+
 // y = x converted between complex double and the Krylov basis type.
 template <typename A, typename B>
 __global__ void k_cvt(int64_t N, const C2<A>* __restrict__ x, C2<B>* __restrict__ y) {
@@ -460,13 +493,43 @@ static void back_substitute(const Cycle& cy, int j, std::vector<zc>& y) {
   }
 }
 
+// The unscaled residual ||b - Z x_j|| of the cycle's current iterate, from
+// the small problem: its residual in the rotated frame is g_{j+1} e_{j+1};
+// rotated back (G_j^H .. G_0^H) it gives coefficients a over V[0..j+1], the
+// scaled residual is V a and the residual D^-1 V a (exact in exact
+// arithmetic; each cycle's true residual is recomputed with a product).
+template <typename B>
+static pie_status unscaled_residual(Ctx& c, const C2<B>* V, const Cycle& cy, int j, double* out) {
+  std::vector<zc> a(j + 2, zc(0));
+  a[j + 1] = cy.g[j + 1];
+  for (int i = j; i >= 0; --i) {
+    const zc ai = a[i], aj = a[i + 1];
+    a[i] = cy.cs[i] * ai - std::conj(cy.sn[i]) * aj;
+    a[i + 1] = cy.sn[i] * ai + std::conj(cy.cs[i]) * aj;
+  }
+  pie_status s = to_dev(c, a, j + 2);
+  if (s != PIE_OK) return s;
+  const unsigned blocks = nb_(c.N, kRedThreads);
+  k_resnorm<B><<<blocks, kRedThreads, sizeof(cd) * (j + 2), c.st>>>(c.N, j + 2, V, c.N, c.hdev, c.d, c.partial);
+  k_mdot_finish<<<1, 32, 0, c.st>>>(1, int(blocks), c.partial, c.hdev + c.hcap - 1);
+  cd r;
+  s = cuda_check(cudaMemcpyAsync(&r, c.hdev + c.hcap - 1, sizeof(cd), cudaMemcpyDeviceToHost, c.st), "residual");
+  if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "residual sync");
+  *out = std::sqrt(r.x);
+  return s;
+}
+
 // One GMRES cycle (no restart) on the scaled operator D Op D, x0 = 0, with
 // V[0] = D r / ||D r|| given: Arnoldi up to m steps or until the rotated
 // residual falls below stop_abs.  On return y (host) holds the coefficients
 // and j the number of steps.
+// With check_every > 0, every check_every steps the unscaled residual of the
+// iterate (unscaled_residual) is formed as well and the cycle also ends when
+// it falls to stop_unscaled.
 template <typename B>
 static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, Cycle& cy, double beta, double stop_abs, int max_steps,
-                                int& j_out, std::vector<zc>& y, bool& breakdown, int& steps_done) {
+                                int& j_out, std::vector<zc>& y, bool& breakdown, int& steps_done,
+                                int check_every = 0, double stop_unscaled = 0) {
   const int64_t N = c.N;
   const int m = cy.m;
   pie_status s = PIE_OK;
@@ -490,6 +553,14 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, Cycle& cy, double beta, double
     if (std::abs(cy.g[j + 1]) <= stop_abs) {
       ++j;
       break;
+    }
+    if (check_every > 0 && (j + 1) % check_every == 0) {
+      double ru = 0;
+      if ((s = unscaled_residual<B>(c, V, cy, j, &ru)) != PIE_OK) return s;
+      if (ru <= stop_unscaled) {
+        ++j;
+        break;
+      }
     }
   }
   back_substitute(cy, j, y);
@@ -584,7 +655,8 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
     int j = 0;
     bool breakdown = false;
     const double dbn = beta / rel;  // scale of ||D b|| for the cycle's stopping estimate
-    if ((s = arnoldi_cycle<B>(c, V, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, breakdown, it)) != PIE_OK)
+    if ((s = arnoldi_cycle<B>(c, V, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, breakdown, it, 4, tol * bn)) !=
+        PIE_OK)
       return s;
     // x += D (sum_j y_j V_j), in complex double
     if ((s = to_dev(c, y, j)) != PIE_OK) return s;
@@ -753,7 +825,15 @@ static pie_status nested_t(Problem& po, Problem& pi, const cd* b, cd* x, const p
           break;
         }
         k_axs<double><<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / hn, w, w);
-        if (std::abs(cyo.g[j + 1]) <= 0.5 * np.tol * dbn) {
+        // the scaled estimate, or the unscaled residual of the iterate,
+        // reaching tol ends the cycle; the true residual then decides
+        if (std::abs(cyo.g[j + 1]) <= np.tol * dbn) {
+          ++j;
+          break;
+        }
+        double ru = 0;
+        if ((s = unscaled_residual<double>(co, Vo, cyo, j, &ru)) != PIE_OK) return s;
+        if (ru <= np.tol * bn) {
           ++j;
           break;
         }

@@ -248,13 +248,19 @@ def complex_normal(shape, seed: int) -> np.ndarray:
     return (re + 1j * im).astype(np.complex128)
 
 
-def balanced_vector(n_rwg: int, n_tri: int, seed: int, sigma_scale: float) -> np.ndarray:
-    """Complex normal excitation vector in mesh order [RWG ; pulse], with the
-    pulse part multiplied by sigma_scale so that both blocks of the operator
-    contribute at comparable magnitude."""
-    x = complex_normal(n_rwg + n_tri, seed)
-    x[n_rwg:] *= sigma_scale
-    return x
+def planewave_set():
+    """The 64 plane waves of the batched and gradient workloads: propagation
+    directions -r(theta, phi) on a uniform grid, theta at the midpoints of 4
+    equal bands of [0, pi] and phi at 8 steps of pi/4, each with the theta
+    and the phi polarisation.  Returns a list of (khat [3], pol [3])."""
+    waves = []
+    for t in (np.arange(4) + 0.5) * np.pi / 4:
+        for p in np.arange(8) * 2 * np.pi / 8:
+            kh = -np.array([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)])
+            e_th = np.array([np.cos(t) * np.cos(p), np.cos(t) * np.sin(p), -np.sin(t)])
+            e_ph = np.array([-np.sin(p), np.cos(p), 0.0])
+            waves += [(kh, e_th), (kh, e_ph)]
+    return waves
 
 
 def bistatic_directions(n: int = 181, phi: float = 0.0) -> np.ndarray:

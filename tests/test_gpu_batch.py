@@ -139,3 +139,38 @@ def test_group_rejects_bad_arguments(pg):
         grp.apply(xs, ys)
     assert ei.value.code == 1
     mem[1].profile_end()
+
+
+def test_group_products_match_dense_oracle(pg):
+    """Section 8(f2)'s multi-mesh launch against the oracle itself, not only
+    against the members' own products: three meshes of uneven size (sphere,
+    cube with its faces on box planes, 2:1:1 ellipsoid; 320 / 1536 / 512
+    triangles), two right-hand sides each (RWG sources alone, pulse sources
+    alone), one graph launch; every member's every column within 1e-3 of the
+    oracle's dense Galerkin product per block (the accuracy of Eqs. (4)-(5)
+    at the default parameters)."""
+    import torch
+    from oracle.dense import assemble
+    from oracle.mesh import build_topology
+    meshes = [(pi.icosphere(2), 2.0), (pi.cube(8), 1.0), (pi.octasphere(3, (1.0, 0.5, 0.5)), 0.0)]
+    members, dense = [], []
+    for (xyz, tri), side in meshes:
+        members.append(pg.Problem(pg.Mesh(xyz, tri), K, 3, root_side=side, precision=pg.PIE_MIXED, max_nrhs=2))
+        dense.append(assemble(build_topology(xyz, tri), K))
+    assert len({m.T for m in members}) == 3
+    xs = []
+    for i, m in enumerate(members):
+        cols = [np.r_[pi.complex_normal(m.E, 40 + i), np.zeros(m.T)], np.r_[np.zeros(m.E), pi.complex_normal(m.T, 50 + i)]]
+        xs.append(torch.from_numpy(np.stack(cols)).cuda())
+    ys = [torch.empty_like(x) for x in xs]
+    grp = pg.Group(members)
+    grp.apply(xs, ys)
+    torch.cuda.synchronize()
+    assert grp.info()["graphs"] == 1
+    for m, Z, x, y in zip(members, dense, xs, ys):
+        X, Y = x.cpu().numpy(), y.cpu().numpy()
+        for j in range(2):
+            yd = Z @ X[j]
+            for sl in (slice(0, m.E), slice(m.E, None)):
+                err = np.linalg.norm(Y[j][sl] - yd[sl]) / np.linalg.norm(yd[sl])
+                assert err < 1e-3, (m.T, j, err)

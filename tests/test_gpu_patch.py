@@ -38,3 +38,48 @@ def test_patch_levels_agree(freq):
         dev = np.max(np.abs(fields[L][mask] - ref[mask]))
         print(freq, L, "max deviation from 6 levels (dB)", dev)
         assert dev < 0.3
+
+
+def test_patch_standard_diagonalization_matches_oracle():
+    """The capped scale factor of the Fig. 1 study at 100 MHz: boxes larger
+    than x / k0 in wavelengths use s = 1 (the standard diagonalization of
+    Eq. (4)), here at every level of a 200-triangle patch at 3 levels (leaf
+    0.15 m, k0 a = 0.31 > 0.08) and an 800-triangle one at 4 levels.  GPU stages against the oracle MLFMA with the same
+    scale factors per level and component to 1e-12, the product against it
+    within 4 x the oracle's own sensitivity to one-ulp changes of its
+    angular nodes, and against the oracle's dense product to 1e-3 per
+    block."""
+    import torch
+    from oracle.dense import assemble
+    from tests._lib import ensure_built
+    from tests._sensitivity import node_sensitivity
+    ensure_built()
+    import paper_1806_04164_gb300 as pg
+    from oracle.mlfma import MLFMA
+    k = 2 * np.pi * 1e8 / 299792458.0
+    for n, L in ((10, 3), (20, 4)):
+        xyz, tri = pi.square_patch(n)
+        M = MLFMA(xyz, tri, k, L)
+        assert all(M.scale[l] == 1.0 for l in range(3, L + 1))
+        pr = pg.Problem(pg.Mesh(xyz, tri), k, L)
+        x = pi.complex_normal(pr.N, 9)
+        y = pr.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+        yo, st = M.apply(x, stages=True)
+        rel = lambda a, b: np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+        for l in range(3, L + 1):
+            # per component against the level's pattern norm (the flat patch
+            # radiates no z current: that component is zero on both sides)
+            S, G = pr.stage(0, l), pr.stage(1, l)
+            nS, nG = np.linalg.norm(st["S"][l]), np.linalg.norm(st["G"][l])
+            for c in range(5):
+                assert np.linalg.norm(S[:, c] - st["S"][l][:, c]) <= 1e-12 * nS, ("S", L, l, c)
+                assert np.linalg.norm(G[:, c] - st["G"][l][:, c]) <= 1e-12 * nG, ("G", L, l, c)
+        sens, _, _ = node_sensitivity(xyz, tri, k, L, x, side=0.0)
+        print(f"patch L={L}: GPU vs oracle {rel(y, yo):.2e}, node sensitivity {sens:.2e}")
+        assert rel(y, yo) <= 4 * sens + 1e-13
+        Z = assemble(M.top, k)
+        for xx in (np.r_[pi.complex_normal(pr.E, 1), np.zeros(pr.T)], np.r_[np.zeros(pr.E), pi.complex_normal(pr.T, 2)]):
+            ym = pr.apply(torch.from_numpy(xx).cuda()).cpu().numpy()
+            yd = Z @ xx
+            for sl in (slice(0, pr.E), slice(pr.E, None)):
+                assert rel(ym[sl], yd[sl]) < 1e-3, (L, rel(ym[sl], yd[sl]))

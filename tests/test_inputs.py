@@ -32,3 +32,18 @@ def test_patch_is_open():
     top = build_topology(xyz, tri)
     assert top.T == 11250 and top.E == 3 * 75 * 75 - 2 * 75
     assert np.all(top.normal[:, 2] > 0.999)
+
+
+def test_planewave_set():
+    """64 waves: 32 distinct unit directions, two unit polarisations each,
+    both orthogonal to the direction and to each other."""
+    w = pi.planewave_set()
+    assert len(w) == 64
+    dirs = {tuple(np.round(k, 12)) for k, _ in w}
+    assert len(dirs) == 32
+    for i in range(0, 64, 2):
+        (k, e1), (k2, e2) = w[i], w[i + 1]
+        assert np.allclose(k, k2)
+        for v in (k, e1, e2):
+            assert abs(np.linalg.norm(v) - 1) < 1e-14
+        assert abs(k @ e1) < 1e-14 and abs(k @ e2) < 1e-14 and abs(e1 @ e2) < 1e-14
