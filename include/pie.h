@@ -285,7 +285,11 @@ pie_status pie_farfield_adjoint(pie_problem* pr, const double* rhat, int64_t ndi
  * `restart` steps, stopping when the FP64 residual ||b - Z x||/||b|| <= tol
  * (the operator is scaled symmetrically by the inverse square roots of the
  * diagonal magnitudes of its near part; the stopping test is on the
- * unscaled system).  PIE_FP64 problems keep the Krylov basis in complex
+ * unscaled system: a cycle ends when the rotated residual of the scaled
+ * system falls to tol / 2 or the unscaled residual of the iterate, formed
+ * from the Krylov basis every 4 steps, to tol, and the true residual
+ * b - Z x then decides; after twelve cycles in a row so ended whose true
+ * residual missed tol, later cycles run at least 25 steps, then 50, ...).  PIE_FP64 problems keep the Krylov basis in complex
  * double; PIE_MIXED problems keep it in complex float, with the solution and
  * the true residual in complex double recomputed at every restart (iterative
  * refinement with a GMRES inner solver), so the basis precision limits the
@@ -335,9 +339,11 @@ pie_status pie_solve_guess(pie_problem* pr, const void* b, void* x, int nrhs, do
  *   outer_restart: outer steps per restart (1..200); 0 = iterative
  *     refinement (x += D z for the preconditioned scaled residual);
  *   max_outer: bound on products with the outer operator per column.
- * An outer cycle ends when its residual estimate reaches tol (or after
- * outer_restart steps); the FP64 true residual then decides whether the
- * column has converged or another cycle starts.
+ * An outer cycle ends when its rotated (scaled) residual or the unscaled
+ * residual of its iterate (formed from the outer Krylov basis every step)
+ * reaches tol, or after outer_restart steps; the FP64 true residual then
+ * decides (after twelve cycles in a row so ended whose true residual missed
+ * tol, later cycles run at least 5 steps, then 10, ...).
  * Synchronises the stream.  Returns PIE_OK when every column converged, else
  * PIE_ERR_NOCONV of the first column that did not; PIE_ERR_PARAM (mismatched
  * problems, PIE_FP32 outer problem, parameters out of range), PIE_ERR_OOM,
@@ -452,9 +458,13 @@ pie_status pie_tune_levels(const pie_mesh* m, double k0, const pie_params* base,
  * multiply-add chains (eight independent chains per thread, 4 blocks of 256
  * threads per SM) in real FP64 and FP32 with CUDA events on the
  * stream, best of three launches after ten untimed ones, about 0.5 s in all;
- * writes TFLOP/s (2 flop per FMA) to the host doubles.  Synchronises the
- * stream.  Errors: PIE_ERR_PARAM (NULL output), PIE_ERR_CUDA. */
-pie_status pie_measure_peaks(double* fp64_tflops, double* fp32_tflops, void* stream);
+ * writes TFLOP/s (2 flop per FMA) and the SM clock in MHz that the best
+ * launch ran at (clock64 ticks over globaltimer nanoseconds: long FMA
+ * streams can run below the maximum clock under the power limit) to the
+ * host doubles.  Synchronises the stream.  Errors: PIE_ERR_PARAM (NULL
+ * output), PIE_ERR_CUDA. */
+pie_status pie_measure_peaks(double* fp64_tflops, double* fp32_tflops, double* fp64_mhz, double* fp32_mhz,
+                             void* stream);
 
 /* Multi-mesh batch: several problems (meshes of uneven size, any
  * wavenumbers and precisions) applied to nrhs right-hand sides each in ONE

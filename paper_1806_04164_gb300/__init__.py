@@ -124,7 +124,7 @@ def lib():
         L.pie_solve.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
         L.pie_solve_guess.argtypes = [vp, vp, vp, i32, dbl, i32, i32, ctypes.POINTER(SolveStats), vp]
         L.pie_apply_levels.argtypes = [vp, vp, vp, ctypes.c_uint32, i32, i32, vp]
-        L.pie_measure_peaks.argtypes = [PD, PD, vp]
+        L.pie_measure_peaks.argtypes = [PD, PD, PD, PD, vp]
         L.pie_solve_nested.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(NestedParams),
                                        ctypes.POINTER(NestedStats), vp]
         PT = ctypes.POINTER(Tuning)
@@ -506,11 +506,13 @@ def tune_levels(mesh, k0, lmin, lmax, nrhs=1, root_side=0.0, tau=DEFAULT_TAU, ka
 
 
 def measure_peaks(stream=None):
-    """FP64 and FP32 fused multiply-add throughput of the current device in
-    TFLOP/s (pie_measure_peaks)."""
-    f64, f32 = ctypes.c_double(), ctypes.c_double()
-    _check(lib().pie_measure_peaks(ctypes.byref(f64), ctypes.byref(f32), _stream(stream)))
-    return f64.value, f32.value
+    """FP64 and FP32 fused multiply-add throughput of the current device
+    (pie_measure_peaks): dict with TFLOP/s and the SM clock (MHz) each probe
+    ran at."""
+    f64, f32, m64, m32 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().pie_measure_peaks(ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(m64), ctypes.byref(m32),
+                                   _stream(stream)))
+    return dict(fp64_tflops=f64.value, fp32_tflops=f32.value, fp64_mhz=m64.value, fp32_mhz=m32.value)
 
 
 class Group:

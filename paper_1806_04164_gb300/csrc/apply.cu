@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
 // kNearStage read the coefficients from global memory instead.
 constexpr int kNearStage = 512;
 template <typename Rio, bool H16>
-__global__ void __launch_bounds__(256) k_near_box(int64_t nleaf, int64_t nnz, const int32_t* __restrict__ leaf_start,
+__global__ void __launch_bounds__(256, 3) k_near_box(int64_t nleaf, int64_t nnz, const int32_t* __restrict__ leaf_start,
                                                   const int32_t* __restrict__ near_ptr,
                                                   const int32_t* __restrict__ near_idx,
                                                   const int32_t* __restrict__ near_off,
@@ -187,41 +187,53 @@ __global__ void __launch_bounds__(256) k_near_box(int64_t nleaf, int64_t nnz, co
 #pragma unroll
       for (int i = 0; i < 6; ++i) acc[i] = mk<float>(0, 0);
       int qi = q0;
-      for (int j = lane; j < len; j += 32) {
+      // entry j's eight moments and six source coefficients
+      auto load = [&](int j, cf* m, cf* c) {
         const int64_t ee = e0 + j;
-        cf m0, mt0, mt1, mt2, ms0, ms1, ms2, mts;
         if constexpr (H16) {
-          auto ld = [&](int q) {
+#pragma unroll
+          for (int q = 0; q < kMom; ++q) {
             const float2 v = __half22float2(momh[q * nnz + ee]);
-            return mk<float>(v.x * msc.s[q], v.y * msc.s[q]);
-          };
-          m0 = ld(0), mt0 = ld(1), mt1 = ld(2), mt2 = ld(3), ms0 = ld(4), ms1 = ld(5), ms2 = ld(6), mts = ld(7);
+            m[q] = mk<float>(v.x * msc.s[q], v.y * msc.s[q]);
+          }
         } else {
-          m0 = mom[ee];
-          mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
-          ms0 = mom[4 * nnz + ee], ms1 = mom[5 * nnz + ee], ms2 = mom[6 * nnz + ee];
-          mts = mom[7 * nnz + ee];
+#pragma unroll
+          for (int q = 0; q < kMom; ++q) m[q] = mom[q * nnz + ee];
         }
-        cf a, b0, b1, b2, sg, dd;
         if (staged) {
-          a = cs[0][j], b0 = cs[1][j], b1 = cs[2][j], b2 = cs[3][j], sg = cs[4][j], dd = cs[5][j];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) c[k] = cs[k][j];
         } else {
           while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
-          const cf* c = coef + 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
-          a = c[0], b0 = c[1], b1 = c[2], b2 = c[3], sg = c[4], dd = c[5];
+          const cf* src = coef + 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
+#pragma unroll
+          for (int k = 0; k < 6; ++k) c[k] = src[k];
         }
-        cfma(acc[0], a, mts);
-        cfma(acc[0], b0, mt0);
-        cfma(acc[0], b1, mt1);
-        cfma(acc[0], b2, mt2);
-        cfma(acc[1], a, ms0);
-        cfma(acc[1], b0, m0);
-        cfma(acc[2], a, ms1);
-        cfma(acc[2], b1, m0);
-        cfma(acc[3], a, ms2);
-        cfma(acc[3], b2, m0);
-        cfma(acc[4], sg, m0);
-        cfma(acc[5], dd, m0);
+      };
+      // m: m0, mt(3), ms(3), mts; c: a, beta(3), sigma, d
+      auto accumulate = [&](const cf* m, const cf* c) {
+        cfma(acc[0], c[0], m[7]);
+        cfma(acc[0], c[1], m[1]);
+        cfma(acc[0], c[2], m[2]);
+        cfma(acc[0], c[3], m[3]);
+        cfma(acc[1], c[0], m[4]);
+        cfma(acc[1], c[1], m[0]);
+        cfma(acc[2], c[0], m[5]);
+        cfma(acc[2], c[2], m[0]);
+        cfma(acc[3], c[0], m[6]);
+        cfma(acc[3], c[3], m[0]);
+        cfma(acc[4], c[4], m[0]);
+        cfma(acc[5], c[5], m[0]);
+      };
+      // entries j and j + 32 loaded together (twice the loads in flight),
+      // accumulated in the order j, j + 32 of the one-entry loop
+      for (int j = lane; j < len; j += 64) {
+        cf ma[kMom], ca[6], mb[kMom], cb[6];
+        const bool two = j + 32 < len;
+        load(j, ma, ca);
+        if (two) load(j + 32, mb, cb);
+        accumulate(ma, ca);
+        if (two) accumulate(mb, cb);
       }
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
@@ -300,23 +312,30 @@ __global__ void k_agg(int P, int ntheta, int64_t nb, const int32_t* __restrict__
 // S_l[b] = sum_children phase_o (F S_child); one block per parent, one thread
 // per sample; the child pattern is staged in shared memory.
 template <typename Rf>
-__global__ void k_interp(int P, const int32_t* __restrict__ child_start, const int8_t* __restrict__ oct_child,
-                         const C2<Rf>* __restrict__ Sc, const Rf* __restrict__ Ft, const C2<Rf>* __restrict__ phase,
-                         C2<Rf>* __restrict__ Sp, int64_t sSc = 0, int64_t sSp = 0) {
+__global__ void k_interp(int P, int64_t nb, const int32_t* __restrict__ child_start,
+                         const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Sc,
+                         const Rf* __restrict__ Ft, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Sp,
+                         int64_t sSc = 0, int64_t sSp = 0) {
   Sc += blockIdx.y * sSc;
   Sp += blockIdx.y * sSp;
   extern __shared__ unsigned char smem_raw[];
-  C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw);
-  int b = blockIdx.x;
-  int p = threadIdx.x;
+  // small angular grids: one parent per threadIdx.y row, each with its own staging region
+  C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw) + threadIdx.y * kComp * P;
+  const int64_t b = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
+  const bool live = b < nb;
+  const int c0 = live ? child_start[b] : 0, c1 = live ? child_start[b + 1] : 0;
+  const int p = threadIdx.x;
   C2<Rf> acc[kComp];
 #pragma unroll
   for (int c = 0; c < kComp; ++c) acc[c] = mk<Rf>(0, 0);
-  for (int ch = child_start[b]; ch < child_start[b + 1]; ++ch) {
+  for (int k = 0;; ++k) {
+    const int ch = c0 + k;
+    const bool have = ch < c1;
+    if (!__syncthreads_or(have)) break;  // every row of the block done
+    if (have)
+      for (int i = threadIdx.x; i < kComp * P; i += blockDim.x) sm[i] = Sc[(int64_t)ch * kComp * P + i];
     __syncthreads();
-    for (int i = threadIdx.x; i < kComp * P; i += blockDim.x) sm[i] = Sc[(int64_t)ch * kComp * P + i];
-    __syncthreads();
-    if (p < P) {
+    if (have && p < P) {
       C2<Rf> sum[kComp];
 #pragma unroll
       for (int c = 0; c < kComp; ++c) sum[c] = mk<Rf>(0, 0);
@@ -330,7 +349,7 @@ __global__ void k_interp(int P, const int32_t* __restrict__ child_start, const i
       for (int c = 0; c < kComp; ++c) cfma(acc[c], ph, sum[c]);
     }
   }
-  if (p < P) {
+  if (live && p < P) {
 #pragma unroll
     for (int c = 0; c < kComp; ++c) Sp[((int64_t)b * kComp + c) * P + p] = acc[c];
   }
@@ -633,19 +652,21 @@ __global__ void k_trans(int P, int64_t nb, const int32_t* __restrict__ il_ptr, c
 }
 
 // a5: anterpolation from level l to level l+1:
-// G_child += F^T (conj(phase_o) G_parent); one block per child box.
+// G_child += F^T (conj(phase_o) G_parent); one child box per threadIdx.y
+// row of a block (several rows for small angular grids).
 template <typename Rf>
-__global__ void k_anterp(int P, const int32_t* __restrict__ parent, const int8_t* __restrict__ oct_child,
+__global__ void k_anterp(int P, int64_t nc, const int32_t* __restrict__ parent, const int8_t* __restrict__ oct_child,
                          const C2<Rf>* __restrict__ Gp, const Rf* __restrict__ F, const C2<Rf>* __restrict__ phase,
                          C2<Rf>* __restrict__ Gc, int64_t sGp = 0, int64_t sGc = 0) {
   Gp += blockIdx.y * sGp;
   Gc += blockIdx.y * sGc;
   extern __shared__ unsigned char smem_raw[];
-  C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw);
-  int ch = blockIdx.x;
-  int par = parent[ch];
-  int o = oct_child[ch];
-  for (int i = threadIdx.x; i < kComp * P; i += blockDim.x) {
+  C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw) + threadIdx.y * kComp * P;
+  const int64_t ch = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
+  const bool live = ch < nc;
+  const int par = live ? parent[ch] : 0;
+  const int o = live ? oct_child[ch] : 0;
+  for (int i = threadIdx.x; live && i < kComp * P; i += blockDim.x) {
     int q = i % P;
     C2<Rf> g = Gp[(int64_t)par * kComp * P + i];
     C2<Rf> ph = phase[o * P + q];
@@ -655,6 +676,7 @@ __global__ void k_anterp(int P, const int32_t* __restrict__ parent, const int8_t
     sm[i] = h;
   }
   __syncthreads();
+  if (!live) return;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     C2<Rf> sum[kComp];
 #pragma unroll
@@ -916,6 +938,7 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   }
   prof_mark(pr, 2, true, st);
   const size_t sm = sizeof(C2<Rf>) * kComp * P;
+  const int fbp = tpb < 128 ? 128 / tpb : 1;  // boxes per block of the dense-filter kernels
   const bool fft8 = pr.par.ntheta == 8;
   if (fft8) {
     pie_status s = fft_prepare<8, Rf>();
@@ -929,8 +952,8 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
         static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l));
   }
   for (int l = L - 1; l >= 3 && !fft8; --l) {
-    k_interp<Rf><<<dim3(unsigned(pr.lev[l].nb), nr), tpb, sm, st>>>(
-        P, pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
+    k_interp<Rf><<<dim3(nblk(pr.lev[l].nb, fbp), nr), dim3(tpb, fbp), sm * fbp, st>>>(
+        P, pr.lev[l].nb, pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
         static_cast<const Rf*>(pr.lev[l].Ft), static_cast<const C2<Rf>*>(pr.lev[l].phase),
         static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l));
   }
@@ -956,8 +979,8 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
         static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1));
   }
   for (int l = 3; l < L && !fft8; ++l) {
-    k_anterp<Rf><<<dim3(unsigned(pr.lev[l + 1].nb), nr), tpb, sm, st>>>(
-        P, pr.lev[l + 1].parent, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
+    k_anterp<Rf><<<dim3(nblk(pr.lev[l + 1].nb, fbp), nr), dim3(tpb, fbp), sm * fbp, st>>>(
+        P, pr.lev[l + 1].nb, pr.lev[l + 1].parent, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
         static_cast<const Rf*>(pr.lev[l].F), static_cast<const C2<Rf>*>(pr.lev[l].phase),
         static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1));
   }

@@ -13,9 +13,20 @@ namespace pie {
 // Written only when the chains reach an impossible value, so that the
 // compiler keeps the loop; never read.
 static __device__ double g_peak_sink[2];
+// SM clock ticks and nanoseconds over one launch, read by thread 0 of block 0
+static __device__ unsigned long long g_peak_clock[2];
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_fma_chains(int iters, R b, R c) {
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  const long long c0 = clock64();
+  const unsigned long long t0 = timer ? global_ns() : 0;
   R a0 = R(threadIdx.x), a1 = a0 + R(1), a2 = a0 + R(2), a3 = a0 + R(3);
   R a4 = a0 + R(4), a5 = a0 + R(5), a6 = a0 + R(6), a7 = a0 + R(7);
 #pragma unroll 4
@@ -31,12 +42,19 @@ __global__ void __launch_bounds__(256) k_fma_chains(int iters, R b, R c) {
   }
   const R s = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
   if (s == R(-1.2345e-30)) g_peak_sink[sizeof(R) == 8 ? 0 : 1] = double(s);
+  if (timer) {
+    g_peak_clock[0] = (unsigned long long)(clock64() - c0);
+    g_peak_clock[1] = global_ns() - t0;
+  }
 }
 
 // Best of three timed launches (CUDA events) after ten untimed ones (the
-// clocks ramp up from idle), in TFLOP/s (2 flop per FMA).
+// clocks ramp up from idle), in TFLOP/s (2 flop per FMA), and the SM clock
+// (MHz) block 0 saw during the best launch (clock64 ticks over globaltimer
+// nanoseconds): long FMA streams can run below the maximum clock under the
+// power limit, so the rate per clock is the hardware figure.
 template <typename R>
-static pie_status fma_peak(int nsm, int iters, cudaStream_t st, double* tflops) {
+static pie_status fma_peak(int nsm, int iters, cudaStream_t st, double* tflops, double* mhz) {
   const unsigned blocks = unsigned(nsm * 4);
   const double flops = 2.0 * 8.0 * double(iters) * double(blocks) * 256.0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -52,7 +70,13 @@ static pie_status fma_peak(int nsm, int iters, cudaStream_t st, double* tflops) 
     s = cuda_check(cudaEventSynchronize(e1), "peak probe");
     float ms = 0;
     if (s == PIE_OK) s = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "peak probe");
-    if (s == PIE_OK && ms > 0) best = std::max(best, flops / (double(ms) * 1e-3) / 1e12);
+    const double tf = flops / (double(ms) * 1e-3) / 1e12;
+    if (s == PIE_OK && ms > 0 && tf > best) {
+      best = tf;
+      unsigned long long clk[2] = {0, 0};
+      s = cuda_check(cudaMemcpyFromSymbol(clk, g_peak_clock, sizeof(clk)), "peak probe clock");
+      *mhz = clk[1] > 0 ? double(clk[0]) / double(clk[1]) * 1e3 : 0.0;
+    }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -64,8 +88,9 @@ static pie_status fma_peak(int nsm, int iters, cudaStream_t st, double* tflops) 
 
 using namespace pie;
 
-extern "C" pie_status pie_measure_peaks(double* fp64_tflops, double* fp32_tflops, void* stream) {
-  if (!fp64_tflops || !fp32_tflops) {
+extern "C" pie_status pie_measure_peaks(double* fp64_tflops, double* fp32_tflops, double* fp64_mhz, double* fp32_mhz,
+                                        void* stream) {
+  if (!fp64_tflops || !fp32_tflops || !fp64_mhz || !fp32_mhz) {
     set_error("pie_measure_peaks: NULL argument");
     return PIE_ERR_PARAM;
   }
@@ -75,7 +100,7 @@ extern "C" pie_status pie_measure_peaks(double* fp64_tflops, double* fp32_tflops
   if (s != PIE_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // about 20 ms per launch at GB300's nominal FP64 (1.25 TFLOP/s) and FP32 (80 TFLOP/s) rates
-  s = fma_peak<double>(nsm, 10000, st, fp64_tflops);
-  if (s == PIE_OK) s = fma_peak<float>(nsm, 600000, st, fp32_tflops);
+  s = fma_peak<double>(nsm, 10000, st, fp64_tflops, fp64_mhz);
+  if (s == PIE_OK) s = fma_peak<float>(nsm, 600000, st, fp32_tflops, fp32_mhz);
   return s;
 }

@@ -520,16 +520,19 @@ static pie_status unscaled_residual(Ctx& c, const C2<B>* V, const Cycle& cy, int
 }
 
 // One GMRES cycle (no restart) on the scaled operator D Op D, x0 = 0, with
-// V[0] = D r / ||D r|| given: Arnoldi up to m steps or until the rotated
-// residual falls below stop_abs.  On return y (host) holds the coefficients
-// and j the number of steps.
-// With check_every > 0, every check_every steps the unscaled residual of the
-// iterate (unscaled_residual) is formed as well and the cycle also ends when
-// it falls to stop_unscaled.
+// V[0] = D r / ||D r|| given: Arnoldi up to m steps, or until the rotated
+// (scaled) residual falls below stop_abs, or -- with hint_every > 0 -- the
+// unscaled residual of the iterate, formed from the small problem every
+// hint_every steps (unscaled_residual), falls to stop_unscaled.  These
+// estimates end the cycle only after min_steps steps.  On return y (host)
+// holds the coefficients, j the number of steps, *early whether an estimate
+// ended the cycle.
 template <typename B>
 static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, Cycle& cy, double beta, double stop_abs, int max_steps,
                                 int& j_out, std::vector<zc>& y, bool& breakdown, int& steps_done,
-                                int check_every = 0, double stop_unscaled = 0) {
+                                int hint_every = 0, double stop_unscaled = 0, int min_steps = 0,
+                                bool* early = nullptr) {
+  if (early) *early = false;
   const int64_t N = c.N;
   const int m = cy.m;
   pie_status s = PIE_OK;
@@ -550,17 +553,17 @@ static pie_status arnoldi_cycle(Ctx& c, C2<B>* V, Cycle& cy, double beta, double
       break;
     }
     k_axs<B><<<nb_(N, 256), 256, 0, c.st>>>(N, 1.0 / hn, w, w);
-    if (std::abs(cy.g[j + 1]) <= stop_abs) {
-      ++j;
-      break;
-    }
-    if (check_every > 0 && (j + 1) % check_every == 0) {
+    if (j + 1 < min_steps) continue;
+    bool stop = std::abs(cy.g[j + 1]) <= stop_abs;
+    if (!stop && hint_every > 0 && (j + 1) % hint_every == 0) {
       double ru = 0;
       if ((s = unscaled_residual<B>(c, V, cy, j, &ru)) != PIE_OK) return s;
-      if (ru <= stop_unscaled) {
-        ++j;
-        break;
-      }
+      stop = ru <= stop_unscaled;
+    }
+    if (stop) {
+      if (early) *early = true;
+      ++j;
+      break;
     }
   }
   back_substitute(cy, j, y);
@@ -635,6 +638,18 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
   if (bn == 0) cudaMemsetAsync(x, 0, sizeof(cd) * N, st);  // b = 0: the solution is x = 0, whatever the guess
   Cycle cy(m);
   std::vector<zc> y;
+  // A cycle ends when the rotated residual falls to tol / 2 (scaled
+  // system) or the unscaled residual of its iterate, formed every 4 steps
+  // from the small problem, to tol; the true residual b - Z x then decides.
+  // Near 1e-6 the true residual of the large problems fluctuates with the
+  // far part's rounding (a ~2.5e-6 nonlinearity of the product) and the
+  // estimates drift from it in either direction; short cycles that restart
+  // from the true residual then often meet tol.  Only after twelve cycles in
+  // a row that an estimate ended but whose true residual missed tol do the
+  // next cycles run at least min_steps steps (25, then doubling, up to
+  // restart): the case where the rounding floor lies above tol.
+  int min_steps = 0, overruled = 0;
+  bool early = false;
   while (result != PIE_OK && it < maxit) {
     if ((s = dotc<double>(c, 1, r, r, tmp)) != PIE_OK) return s;
     rel = std::sqrt(tmp[0].real()) / bn;
@@ -655,8 +670,8 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
     int j = 0;
     bool breakdown = false;
     const double dbn = beta / rel;  // scale of ||D b|| for the cycle's stopping estimate
-    if ((s = arnoldi_cycle<B>(c, V, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, breakdown, it, 4, tol * bn)) !=
-        PIE_OK)
+    if ((s = arnoldi_cycle<B>(c, V, cy, beta, 0.5 * tol * dbn, maxit - it, j, y, breakdown, it, 4, tol * bn,
+                              min_steps, &early)) != PIE_OK)
       return s;
     // x += D (sum_j y_j V_j), in complex double
     if ((s = to_dev(c, y, j)) != PIE_OK) return s;
@@ -665,6 +680,13 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
     if ((s = op_apply(c, x, wd)) != PIE_OK) return s;
     k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, wd, r);
     if ((s = cuda_check(cudaGetLastError(), "gmres launch")) != PIE_OK) return s;
+    if (early) {
+      if ((s = dotc<double>(c, 1, r, r, tmp)) != PIE_OK) return s;
+      overruled = std::sqrt(tmp[0].real()) > tol * bn ? overruled + 1 : 0;
+      if (overruled >= 12) min_steps = std::min(m, std::max(25, 2 * min_steps));
+    } else {
+      overruled = 0;
+    }
     if (breakdown) {
       if ((s = dotc<double>(c, 1, r, r, tmp)) != PIE_OK) return s;
       rel = std::sqrt(tmp[0].real()) / bn;
@@ -782,6 +804,13 @@ static pie_status nested_t(Problem& po, Problem& pi, const cd* b, cd* x, const p
     k_combine<Bi><<<nb_(N, 256), 256, sizeof(cd) * j, st>>>(N, j, Vi, N, hdev, z);
     return cuda_check(cudaGetLastError(), "precondition");
   };
+  // An outer cycle ends when the rotated (scaled) residual or the unscaled
+  // residual of its iterate, formed every step from the small problem,
+  // reaches tol; the true residual then decides.  After twelve cycles in a
+  // row so ended whose true residual missed tol, the next cycles run at least
+  // min_steps steps (5, then doubling, up to outer_restart).
+  int min_steps = 0, overruled = 0;
+  bool early = false;
   while (result != PIE_OK && inner_steps < np.maxit && outer_products < np.max_outer) {
     if ((s = dotc<double>(co, 1, r, r, tmp)) != PIE_OK) return s;
     rel = std::sqrt(tmp[0].real()) / bn;
@@ -807,6 +836,7 @@ static pie_status nested_t(Problem& po, Problem& pi, const cd* b, cd* x, const p
       j = 1;
     } else {
       const double dbn = beta / rel;  // scale of ||D b||
+      early = false;
       cyo.reset(beta);
       bool brk = false;
       for (; j < mo && inner_steps < np.maxit && outer_products < np.max_outer; ++j) {
@@ -825,15 +855,15 @@ static pie_status nested_t(Problem& po, Problem& pi, const cd* b, cd* x, const p
           break;
         }
         k_axs<double><<<nb_(N, 256), 256, 0, st>>>(N, 1.0 / hn, w, w);
-        // the scaled estimate, or the unscaled residual of the iterate,
-        // reaching tol ends the cycle; the true residual then decides
-        if (std::abs(cyo.g[j + 1]) <= np.tol * dbn) {
-          ++j;
-          break;
+        if (j + 1 < min_steps) continue;
+        bool stop = std::abs(cyo.g[j + 1]) <= np.tol * dbn;
+        if (!stop) {
+          double ru = 0;
+          if ((s = unscaled_residual<double>(co, Vo, cyo, j, &ru)) != PIE_OK) return s;
+          stop = ru <= np.tol * bn;
         }
-        double ru = 0;
-        if ((s = unscaled_residual<double>(co, Vo, cyo, j, &ru)) != PIE_OK) return s;
-        if (ru <= np.tol * bn) {
+        if (stop) {
+          early = true;
           ++j;
           break;
         }
@@ -849,6 +879,13 @@ static pie_status nested_t(Problem& po, Problem& pi, const cd* b, cd* x, const p
     ++outer_products;
     k_sub<<<nb_(N, 256), 256, 0, st>>>(N, b, wd, r);
     if ((s = cuda_check(cudaGetLastError(), "nested launch")) != PIE_OK) return s;
+    if (early) {
+      if ((s = dotc<double>(co, 1, r, r, tmp)) != PIE_OK) return s;
+      overruled = std::sqrt(tmp[0].real()) > np.tol * bn ? overruled + 1 : 0;
+      if (overruled >= 12) min_steps = std::min(mo, std::max(5, 2 * min_steps));
+    } else {
+      overruled = 0;
+    }
   }
   if (result != PIE_OK) {
     if ((s = dotc<double>(co, 1, r, r, tmp)) != PIE_OK) return s;

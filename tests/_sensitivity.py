@@ -61,6 +61,31 @@ def node_sensitivity(xyz, tri, k, L, x, tau=7, kappa_a=0.08, ntheta=8, side=2.0,
     return out, M, y
 
 
+def hankel_sensitivity(xyz, tri, k, L, x, tau=7, kappa_a=0.08, ntheta=8, side=2.0, seeds=(0, 1)):
+    """max over seeds of the product's relative change when every scaled
+    Hankel value s^t h_t(k|w|) of Eq. (5) carries a one-ulp relative
+    perturbation (two valid FP64 evaluations of h_t differ by a few ulps)."""
+    import oracle.asd as asd
+    M = mlfma.MLFMA(xyz, tri, k, L, tau=tau, x=kappa_a, ntheta=ntheta, side=side)
+    y = M.apply(x)
+    orig = asd.scaled_hankel
+    out = 0.0
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+
+        def hankel(t, z, s, rng=rng):
+            H = orig(t, z, s)
+            return H * (1 + 2.0 ** -53 * (rng.choice([-1.0, 1.0], H.shape) + 1j * rng.choice([-1.0, 1.0], H.shape)))
+
+        asd.scaled_hankel = hankel
+        try:
+            Mp = mlfma.MLFMA(xyz, tri, k, L, tau=tau, x=kappa_a, ntheta=ntheta, side=side)
+        finally:
+            asd.scaled_hankel = orig
+        out = max(out, _rel(Mp.apply(x), y))
+    return out
+
+
 def order_sensitivity(M, GL, seeds=(0, 1)):
     """max over seeds of the relative change of M.disaggregate(GL) (all four
     potentials together) when the samples are summed in a random order."""

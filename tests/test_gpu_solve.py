@@ -131,6 +131,11 @@ def test_solve_resumes_from_a_guess(pg):
     assert s2["converged"] and s2["rel_residual"] <= 1e-6
     xf, sf = pr.solve(b, tol=1e-6, maxit=2000, restart=100)
     assert s1["iterations"] + s2["iterations"] <= 1.3 * sf["iterations"]
-    assert (torch.linalg.norm(x2 - xf) / torch.linalg.norm(xf)).item() < 1e-4
+    # two solutions at residual 1e-6 differ in x by up to the condition
+    # number times that; their far fields agree far more closely
+    assert (torch.linalg.norm(x2 - xf) / torch.linalg.norm(xf)).item() < 2e-3
+    rh = pi.bistatic_directions(37)
+    E2, Ef = pr.farfield(x2, rh), pr.farfield(xf, rh)
+    assert (torch.linalg.norm(E2 - Ef) / torch.linalg.norm(Ef)).item() < 1e-5
     x3, s3 = pr.solve(b, tol=1e-6, maxit=2000, restart=100, x0=x2)
     assert s3["iterations"] == 0 and torch.equal(x3, x2)
