@@ -36,11 +36,13 @@ METRIC = "PIE MLFMA matvecs/s (1M unk)"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal; used only if the probe fails
 FALLBACK_HBM_GBS = 6800.0
 # DRAM read + write bytes per algorithmic flop of a stage's kernels, from one
-# ncu capture (profiles/); valid while those kernels are unchanged
-NCU_BYTES_PER_FLOP = {}
+# ncu capture (profiles/); valid while those kernels are unchanged.
+# translation: k_trans<double>, one product at icosphere n=6 (levels 3..6),
+# 78.88 MB for 1.3376e9 flop
+NCU_BYTES_PER_FLOP = {"translation": 78.880256e6 / 1.33758976e9}
 # inner operator of the nested solve and its settings
 INNER = dict(tau=3, kappa_a=0.15, ntheta=4)
-NESTED = dict(inner_restart=15, inner_tol=0.1, outer_restart=60, max_outer=400, maxit=8000)
+NESTED = dict(inner_restart=10, inner_tol=0.1, outer_restart=80, max_outer=1000, maxit=12000)
 
 
 def parse():
@@ -61,11 +63,13 @@ def parse():
     ap.add_argument("--gmres-tol", type=float, default=1e-6)
     ap.add_argument("--mesh-level", type=int, default=7,
                     help="icosphere subdivision n (L = n levels); 7 is the timed workload, smaller for profiling")
-    ap.add_argument("--workload", default="1M", choices=["1M", "large", "inner"],
+    ap.add_argument("--workload", default="1M", choices=["1M", "large", "inner", "cpu-oracle"],
                     help="large: the 3,276,800-unknown sphere (n = 8, kR = 1e-4), GMRES time to 1e-6 "
                          "in MIXED and FP64 and 8-right-hand-side product throughput; inner: products of the "
                          "nested solve's complex-float PIE_FP32H operator alone on the icosphere of --mesh-level "
-                         "(for profiling)")
+                         "(for profiling); cpu-oracle: the CPU oracle alone on all host cores (no GPU): "
+                         "GMRES time to 1e-6 on the 1280-triangle sphere at kR = 0.01 and products on the "
+                         "1280- and 81,920-triangle spheres (several minutes)")
     return ap.parse_args()
 
 
@@ -717,6 +721,92 @@ print(json.dumps(out))
 """
 
 
+CPU_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, ROOTDIR)
+import numpy as np
+import pie_inputs as pi
+from oracle.dense import assemble
+from oracle.excitation import rhs_planewave
+from oracle.gmres import gmres
+from oracle.mlfma import MLFMA
+out = {}
+# 1280-triangle sphere, kR = 0.01, L = 3: products and GMRES to 1e-6
+xyz, tri = pi.icosphere(3)
+t0 = time.time()
+M = MLFMA(xyz, tri, 0.01, 3, side=2.0)
+out["setup_s_1280"] = time.time() - t0
+top = M.top
+x = pi.complex_normal(top.N, 1234)
+M.apply(x)
+ts = []
+for _ in range(3):
+    t0 = time.time()
+    M.apply(x)
+    ts.append(time.time() - t0)
+out["mvm_s_1280"] = float(np.median(ts))
+# |Z_ii|^(-1/2) from the pairs of equal or edge-adjacent triangles, the
+# scaling the GPU solver applies
+t0 = time.time()
+adj = [set([t]) for t in range(top.T)]
+for n in range(top.E):
+    a, b = int(top.edge_tri[n, 0]), int(top.edge_tri[n, 1])
+    adj[a].add(b)
+    adj[b].add(a)
+Zp = assemble(top, 0.01, pair_mask=lambda t, s: np.array([int(q) in adj[int(p)] for p, q in zip(t, s)], bool))
+D = 1.0 / np.sqrt(np.abs(np.diag(Zp)))
+out["diag_s_1280"] = time.time() - t0
+b = rhs_planewave(top, 0.01, np.array([0.0, 0.0, -1.0]), np.array([1.0, 0.0, 0.0]))
+nprod = [0]
+def op(v):
+    nprod[0] += 1
+    return D * M.apply(D * v)
+t0 = time.time()
+y, its, hist = gmres(op, D * b, tol=1e-6, restart=100, maxit=1500)
+out["gmres_s_1280"] = time.time() - t0
+out["gmres_iterations_1280"] = int(its)
+out["gmres_products_1280"] = nprod[0]
+xs = D * y
+out["gmres_true_rel_1280"] = float(np.linalg.norm(b - M.apply(xs)) / np.linalg.norm(b))
+out["gmres_scaled_rel_1280"] = float(hist[-1])
+out["N_1280"] = int(top.N)
+if BIG:
+    # 81,920-triangle sphere, kR = 1e-3, L = 6: set-up and one product
+    xyz, tri = pi.icosphere(6)
+    t0 = time.time()
+    M = MLFMA(xyz, tri, 1e-3, 6, side=2.0)
+    out["setup_s_81920"] = time.time() - t0
+    x = pi.complex_normal(M.top.N, 1234)
+    t0 = time.time()
+    M.apply(x)
+    out["mvm_s_81920"] = time.time() - t0
+    out["N_81920"] = int(M.top.N)
+print(json.dumps(out))
+"""
+
+
+def run_cpu_oracle(args):
+    """The CPU FP64 oracle alone on all host cores (numpy with its BLAS on
+    every core), for the small configurations the paper's method is first
+    checked on: the 1280-triangle sphere at kR = 0.01 (3 levels; products,
+    and GMRES(100) to 1e-6 on the system scaled by |Z_ii|^(-1/2), the GPU
+    solver's scaling) and the 81,920-triangle sphere at kR = 1e-3 (6 levels;
+    set-up and one product; left out with --mesh-level below 6).  One JSON
+    line; no GPU work."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    ncpu = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(ncpu), OPENBLAS_NUM_THREADS=str(ncpu), MKL_NUM_THREADS=str(ncpu))
+    code = CPU_ORACLE_SNIPPET.replace("ROOTDIR", repr(ROOT)).replace("BIG", str(args.mesh_level >= 6))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=5400)
+    if out.returncode != 0:
+        print(json.dumps({"workload": "cpu_oracle", "error": (out.stderr.strip().splitlines() or ["failed"])[-1]}))
+        return
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    print(json.dumps({"workload": "cpu_oracle", "kind": "oracle MLFMA (numpy FP64)", "cores": ncpu,
+                      "cpu_model": cpu_model(), **d}))
+
+
 def cpu_model():
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -835,5 +925,7 @@ if __name__ == "__main__":
         run_large(a)
     elif a.workload == "inner":
         run_inner(a)
+    elif a.workload == "cpu-oracle":
+        run_cpu_oracle(a)
     else:
         run_ours(a)

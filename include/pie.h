@@ -67,7 +67,8 @@ typedef enum { PIE_C128 = 0, PIE_C64 = 1 } pie_dtype;
  *            far part in complex double (inputs/outputs PIE_C128);
  *  PIE_FP32H as PIE_FP32, with the near pair moments stored in IEEE half
  *            precision, each of the eight moment planes scaled by its own
- *            power of two (largest magnitude in [2^14, 2^15)) and converted
+ *            power of two (largest magnitude in [2^14, 2^15)), stored
+ *            pair by pair (one 32-byte record per pair) and converted
  *            back to float in the product: half the near-part bytes, a
  *            fixed relative rounding of ~2.4e-4 per moment.  Meant for the
  *            inner operator of pie_solve_nested.
@@ -455,9 +456,10 @@ pie_status pie_tune_levels(const pie_mesh* m, double k0, const pie_params* base,
 
 /* Arithmetic peaks of the current device for the roofline of the ALU-bound
  * kernels (the paper has no counterpart: a measurement aid).  Times fused
- * multiply-add chains (eight independent chains per thread, 4 blocks of 256
- * threads per SM) in real FP64 and FP32 with CUDA events on the
- * stream, best of three launches after ten untimed ones, about 0.5 s in all;
+ * multiply-add chains (eight independent chains per thread, the chain value
+ * either the multiplicand or the addend, 4 or 8 blocks of 256 threads per
+ * SM: the best of the four forms) in real FP64 and FP32 with CUDA events on
+ * the stream, best of three launches after ten untimed ones, about 2 s in all;
  * writes TFLOP/s (2 flop per FMA) and the SM clock in MHz that the best
  * launch ran at (clock64 ticks over globaltimer nanoseconds: long FMA
  * streams can run below the maximum clock under the power limit) to the

@@ -441,8 +441,8 @@ class Problem:
                       product_seconds=s.product_seconds) for s in st[:nrhs]]
         return (x, stats[0]) if b.dim() == 1 else (x, stats)
 
-    def solve_nested(self, b, inner, tol=1e-6, maxit=20000, inner_restart=20, inner_tol=0.1, outer_restart=40,
-                     max_outer=400, stream=None):
+    def solve_nested(self, b, inner, tol=1e-6, maxit=20000, inner_restart=10, inner_tol=0.1, outer_restart=80,
+                     max_outer=1000, stream=None):
         """Nested mixed-precision solve (pie_solve_nested): flexible GMRES on
         this problem's operator, each outer step preconditioned by one GMRES
         cycle on `inner` (a Problem on the same mesh and k0, typically

@@ -386,10 +386,13 @@ pie_status pie_problem_stage(pie_problem* h, int which, int level, double* out, 
       std::vector<__half2> tmp(n);
       s = cuda_check(cudaMemcpy(tmp.data(), src, n * sizeof(__half2), cudaMemcpyDeviceToHost), "stage copy");
       if (s != PIE_OK) return s;
+      // stored pair by pair ([nnz][8]); exported plane by plane like the others
+      const size_t nnz = size_t(pr.nnz);
       for (size_t i = 0; i < n; ++i) {
-        const float sc = pr.mom_scale[i / size_t(pr.nnz)];
-        out[2 * i] = double(__low2float(tmp[i])) * sc;
-        out[2 * i + 1] = double(__high2float(tmp[i])) * sc;
+        const size_t q = i / nnz, e = i % nnz;
+        const __half2 h = tmp[e * kMom + q];
+        out[2 * i] = double(__low2float(h)) * pr.mom_scale[q];
+        out[2 * i + 1] = double(__high2float(h)) * pr.mom_scale[q];
       }
       return PIE_OK;
     }

@@ -52,12 +52,42 @@ __global__ void k_coef(int64_t T, int64_t E, const C2<Rio>* __restrict__ x, cons
   }
 }
 
+// PIE_FP32H pair record: eight half pairs (m0, mt_xyz, ms_xyz, mts) at
+// momh[8 e .. 8 e + 7], 32 bytes, read as two streaming 16-byte loads.
+__device__ __forceinline__ void load_half_record(const __half2* __restrict__ momh, int64_t e, uint4& lo, uint4& hi) {
+  const uint4* p = reinterpret_cast<const uint4*>(momh) + 2 * e;
+  lo = __ldcs(p);
+  hi = __ldcs(p + 1);
+}
+
+// The record's moments in float: each half pair times its plane's scale.
+template <typename Rm>
+__device__ __forceinline__ void unpack_half(const uint4& lo, const uint4& hi, const MomScale& msc, C2<Rm>* m) {
+  const uint32_t w[kMom] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+  for (int q = 0; q < kMom; ++q) {
+    __half2 h;
+    memcpy(&h, &w[q], sizeof(h));
+    const float2 v = __half22float2(h);
+    m[q] = mk<Rm>(Rm(v.x * msc.s[q]), Rm(v.y * msc.s[q]));
+  }
+}
+
+template <typename Rm>
+__device__ __forceinline__ void unpack_half_record(const __half2* __restrict__ momh, int64_t e, const MomScale& msc,
+                                                   C2<Rm>* m) {
+  uint4 lo, hi;
+  load_half_record(momh, e, lo, hi);
+  unpack_half<Rm>(lo, hi, msc, m);
+}
+
 // a1: near part.  One warp per test triangle t; lanes run over the source
 // triangles of the neighbouring leaf boxes (contiguous in tree order), whose
 // eight pair moments are stored plane by plane ([8][nnz]), so a warp reads
 // 32 consecutive entries of each plane (measured faster than per-pair
 // records with vector loads).  Writes pot[t] (initialises it).  H16: the
-// moments come from momh (half pairs, PIE_FP32H) times their plane's scale.
+// moments come from momh (PIE_FP32H: one record of eight half pairs per
+// pair, 32 bytes, two 16-byte loads) times their plane's scale.
 template <typename Rm, typename Rio, int RB = 1, bool H16 = false>
 __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int32_t* __restrict__ leaf_of,
                                               const int32_t* __restrict__ leaf_start,
@@ -94,11 +124,9 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
       const int64_t ee = e0 + j;
       C2<Rm> m0, mt0, mt1, mt2, ms0, ms1, ms2, mts;
       if constexpr (H16) {
-        auto ld = [&](int q) {
-          const float2 v = __half22float2(momh[q * nnz + ee]);
-          return mk<Rm>(Rm(v.x * msc.s[q]), Rm(v.y * msc.s[q]));
-        };
-        m0 = ld(0), mt0 = ld(1), mt1 = ld(2), mt2 = ld(3), ms0 = ld(4), ms1 = ld(5), ms2 = ld(6), mts = ld(7);
+        C2<Rm> m[kMom];
+        unpack_half_record(momh, ee, msc, m);
+        m0 = m[0], mt0 = m[1], mt1 = m[2], mt2 = m[3], ms0 = m[4], ms1 = m[5], ms2 = m[6], mts = m[7];
       } else {
         m0 = mom[ee];
         mt0 = mom[nnz + ee], mt1 = mom[2 * nnz + ee], mt2 = mom[3 * nnz + ee];
@@ -187,19 +215,9 @@ __global__ void __launch_bounds__(256, 3) k_near_box(int64_t nleaf, int64_t nnz,
 #pragma unroll
       for (int i = 0; i < 6; ++i) acc[i] = mk<float>(0, 0);
       int qi = q0;
-      // entry j's eight moments and six source coefficients
-      auto load = [&](int j, cf* m, cf* c) {
-        const int64_t ee = e0 + j;
-        if constexpr (H16) {
-#pragma unroll
-          for (int q = 0; q < kMom; ++q) {
-            const float2 v = __half22float2(momh[q * nnz + ee]);
-            m[q] = mk<float>(v.x * msc.s[q], v.y * msc.s[q]);
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < kMom; ++q) m[q] = mom[q * nnz + ee];
-        }
+      // entry j's six source coefficients (a cursor on the near box that
+      // holds j when they are not staged; j increases call by call)
+      auto coefs = [&](int j, cf* c) {
         if (staged) {
 #pragma unroll
           for (int k = 0; k < 6; ++k) c[k] = cs[k][j];
@@ -225,15 +243,41 @@ __global__ void __launch_bounds__(256, 3) k_near_box(int64_t nleaf, int64_t nnz,
         cfma(acc[4], c[4], m[0]);
         cfma(acc[5], c[5], m[0]);
       };
-      // entries j and j + 32 loaded together (twice the loads in flight),
-      // accumulated in the order j, j + 32 of the one-entry loop
-      for (int j = lane; j < len; j += 64) {
-        cf ma[kMom], ca[6], mb[kMom], cb[6];
-        const bool two = j + 32 < len;
-        load(j, ma, ca);
-        if (two) load(j + 32, mb, cb);
-        accumulate(ma, ca);
-        if (two) accumulate(mb, cb);
+      if constexpr (H16) {
+        // entries j, j + 32, j + 64, j + 96: their 32-byte records loaded
+        // together (four pairs of 16-byte loads in flight per lane), then
+        // accumulated in that order, the order of the one-entry loop
+        constexpr int U = 4;
+        for (int j = lane; j < len; j += 32 * U) {
+          uint4 lo[U], hi[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (j + 32 * u < len) load_half_record(momh, e0 + j + 32 * u, lo[u], hi[u]);
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (j + 32 * u < len) {
+              cf m[kMom], c[6];
+              unpack_half<float>(lo[u], hi[u], msc, m);
+              coefs(j + 32 * u, c);
+              accumulate(m, c);
+            }
+        }
+      } else {
+        // entries j and j + 32 loaded together (twice the loads in flight),
+        // accumulated in the order j, j + 32 of the one-entry loop
+        auto load = [&](int j, cf* m, cf* c) {
+#pragma unroll
+          for (int q = 0; q < kMom; ++q) m[q] = mom[q * nnz + e0 + j];
+          coefs(j, c);
+        };
+        for (int j = lane; j < len; j += 64) {
+          cf ma[kMom], ca[6], mb[kMom], cb[6];
+          const bool two = j + 32 < len;
+          load(j, ma, ca);
+          if (two) load(j + 32, mb, cb);
+          accumulate(ma, ca);
+          if (two) accumulate(mb, cb);
+        }
       }
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
@@ -310,17 +354,27 @@ __global__ void k_agg(int P, int ntheta, int64_t nb, const int32_t* __restrict__
 
 // a3: interpolation from level l+1 to its parents at level l:
 // S_l[b] = sum_children phase_o (F S_child); one block per parent, one thread
-// per sample; the child pattern is staged in shared memory.
+// per sample.  The children's patterns are staged in shared memory cg at a
+// time (all eight when they fit: one load latency per parent instead of one
+// per child), and with fs the filter F^T too (else it is read from global
+// memory); children are summed in order, whatever cg.
 template <typename Rf>
 __global__ void k_interp(int P, int64_t nb, const int32_t* __restrict__ child_start,
                          const int8_t* __restrict__ oct_child, const C2<Rf>* __restrict__ Sc,
                          const Rf* __restrict__ Ft, const C2<Rf>* __restrict__ phase, C2<Rf>* __restrict__ Sp,
-                         int64_t sSc = 0, int64_t sSp = 0) {
+                         int64_t sSc = 0, int64_t sSp = 0, int cg = 1, bool fs = false) {
   Sc += blockIdx.y * sSc;
   Sp += blockIdx.y * sSp;
   extern __shared__ unsigned char smem_raw[];
-  // small angular grids: one parent per threadIdx.y row, each with its own staging region
-  C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw) + threadIdx.y * kComp * P;
+  // the filter (P x P, when fs) first, then one staging region of cg
+  // children per threadIdx.y row (small angular grids: one parent per row)
+  Rf* fsm = reinterpret_cast<Rf*>(smem_raw);
+  const size_t fbytes = fs ? ((sizeof(Rf) * P * P + 15) / 16) * 16 : 0;
+  C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw + fbytes) + threadIdx.y * cg * kComp * P;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  if (fs)
+    for (int i = tid; i < P * P; i += nth) fsm[i] = Ft[i];
+  const Rf* F = fs ? fsm : Ft;
   const int64_t b = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
   const bool live = b < nb;
   const int c0 = live ? child_start[b] : 0, c1 = live ? child_start[b + 1] : 0;
@@ -328,23 +382,24 @@ __global__ void k_interp(int P, int64_t nb, const int32_t* __restrict__ child_st
   C2<Rf> acc[kComp];
 #pragma unroll
   for (int c = 0; c < kComp; ++c) acc[c] = mk<Rf>(0, 0);
-  for (int k = 0;; ++k) {
-    const int ch = c0 + k;
-    const bool have = ch < c1;
-    if (!__syncthreads_or(have)) break;  // every row of the block done
-    if (have)
-      for (int i = threadIdx.x; i < kComp * P; i += blockDim.x) sm[i] = Sc[(int64_t)ch * kComp * P + i];
+  for (int k0 = c0;; k0 += cg) {
+    const int nk = k0 < c1 ? min(cg, c1 - k0) : 0;
+    if (!__syncthreads_or(nk > 0)) break;  // every row of the block done
+    // the nk children are consecutive at level l+1: one contiguous copy
+    for (int i = threadIdx.x; i < nk * kComp * P; i += blockDim.x) sm[i] = Sc[(int64_t)k0 * kComp * P + i];
     __syncthreads();
-    if (have && p < P) {
+    for (int k = 0; k < nk && p < P; ++k) {
+      const C2<Rf>* sk = sm + k * kComp * P;
       C2<Rf> sum[kComp];
 #pragma unroll
       for (int c = 0; c < kComp; ++c) sum[c] = mk<Rf>(0, 0);
+#pragma unroll 4
       for (int q = 0; q < P; ++q) {
-        Rf f = Ft[(int64_t)q * P + p];
+        Rf f = F[(int64_t)q * P + p];
 #pragma unroll
-        for (int c = 0; c < kComp; ++c) rfma(sum[c], f, sm[c * P + q]);
+        for (int c = 0; c < kComp; ++c) rfma(sum[c], f, sk[c * P + q]);
       }
-      C2<Rf> ph = phase[oct_child[ch] * P + p];
+      C2<Rf> ph = phase[oct_child[k0 + k] * P + p];
 #pragma unroll
       for (int c = 0; c < kComp; ++c) cfma(acc[c], ph, sum[c]);
     }
@@ -626,20 +681,42 @@ __global__ void __launch_bounds__(kFftBatch * kComp * NT, 4) k_anterp_fft(
 
 // a4: translation at one level: G[d] = sum_{s in IL(d)} T[off] * S[s];
 // one destination box per threadIdx.y row of a block (several rows for small
-// angular grids), one thread per sample, five components.
+// angular grids), one thread per sample, five components.  In float the
+// list is walked U = 4 entries at a time: their loads are issued together
+// and the multiply-adds follow in list order (the order of the one-entry
+// loop), so a thread waits for one load latency per four entries instead of
+// per entry (the small-grid float levels are latency-bound).  In double the
+// FP64 pipe bounds the kernel and U = 1 (measured: U = 2 was 0.5 % slower).
 template <typename Rf>
 __global__ void k_trans(int P, int64_t nb, const int32_t* __restrict__ il_ptr, const int32_t* __restrict__ il_idx,
                         const int32_t* __restrict__ il_off, const C2<Rf>* __restrict__ Tt,
                         const C2<Rf>* __restrict__ S, C2<Rf>* __restrict__ G, int64_t sS = 0) {
+  constexpr int U = sizeof(Rf) == 4 ? 4 : 1;
   const int64_t d = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
   if (d >= nb) return;
   S += blockIdx.y * sS;
   G += blockIdx.y * sS;
+  const int j0 = il_ptr[d], j1 = il_ptr[d + 1];
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     C2<Rf> acc[kComp];
 #pragma unroll
     for (int c = 0; c < kComp; ++c) acc[c] = mk<Rf>(0, 0);
-    for (int j = il_ptr[d]; j < il_ptr[d + 1]; ++j) {
+    int j = j0;
+    for (; j + U <= j1; j += U) {
+      C2<Rf> tv[U], sv[U][kComp];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        tv[u] = Tt[(int64_t)il_off[j + u] * P + p];
+        const C2<Rf>* src = S + (int64_t)il_idx[j + u] * kComp * P + p;
+#pragma unroll
+        for (int c = 0; c < kComp; ++c) sv[u][c] = src[c * P];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < kComp; ++c) cfma(acc[c], tv[u], sv[u][c]);
+    }
+    for (; j < j1; ++j) {
       int s = il_idx[j];
       C2<Rf> tv = Tt[(int64_t)il_off[j] * P + p];
       const C2<Rf>* src = S + (int64_t)s * kComp * P + p;
@@ -653,15 +730,22 @@ __global__ void k_trans(int P, int64_t nb, const int32_t* __restrict__ il_ptr, c
 
 // a5: anterpolation from level l to level l+1:
 // G_child += F^T (conj(phase_o) G_parent); one child box per threadIdx.y
-// row of a block (several rows for small angular grids).
+// row of a block (several rows for small angular grids).  With fs the
+// filter F is staged in shared memory first (else read from global memory).
 template <typename Rf>
 __global__ void k_anterp(int P, int64_t nc, const int32_t* __restrict__ parent, const int8_t* __restrict__ oct_child,
-                         const C2<Rf>* __restrict__ Gp, const Rf* __restrict__ F, const C2<Rf>* __restrict__ phase,
-                         C2<Rf>* __restrict__ Gc, int64_t sGp = 0, int64_t sGc = 0) {
+                         const C2<Rf>* __restrict__ Gp, const Rf* __restrict__ Fg, const C2<Rf>* __restrict__ phase,
+                         C2<Rf>* __restrict__ Gc, int64_t sGp = 0, int64_t sGc = 0, bool fs = false) {
   Gp += blockIdx.y * sGp;
   Gc += blockIdx.y * sGc;
   extern __shared__ unsigned char smem_raw[];
-  C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw) + threadIdx.y * kComp * P;
+  Rf* fsm = reinterpret_cast<Rf*>(smem_raw);
+  const size_t fbytes = fs ? ((sizeof(Rf) * P * P + 15) / 16) * 16 : 0;
+  C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw + fbytes) + threadIdx.y * kComp * P;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  if (fs)
+    for (int i = tid; i < P * P; i += nth) fsm[i] = Fg[i];
+  const Rf* F = fs ? fsm : Fg;
   const int64_t ch = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
   const bool live = ch < nc;
   const int par = live ? parent[ch] : 0;
@@ -681,6 +765,7 @@ __global__ void k_anterp(int P, int64_t nc, const int32_t* __restrict__ parent, 
     C2<Rf> sum[kComp];
 #pragma unroll
     for (int c = 0; c < kComp; ++c) sum[c] = mk<Rf>(0, 0);
+#pragma unroll 4
     for (int q = 0; q < P; ++q) {
       Rf f = F[(int64_t)q * P + p];
 #pragma unroll
@@ -939,6 +1024,13 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   prof_mark(pr, 2, true, st);
   const size_t sm = sizeof(C2<Rf>) * kComp * P;
   const int fbp = tpb < 128 ? 128 / tpb : 1;  // boxes per block of the dense-filter kernels
+  // dense-filter kernels: the P x P filter in shared memory when it is at
+  // most 16 KB; interpolation stages up to eight children per parent within
+  // 48 KB of shared memory in all
+  const size_t fsb = ((sizeof(Rf) * size_t(P) * P + 15) / 16) * 16;
+  const bool fsh = fsb <= 16384;
+  const size_t fsm_bytes = fsh ? fsb : 0;
+  const int cg = int(std::max<size_t>(1, std::min<size_t>(8, (49152 - fsm_bytes) / (sm * fbp))));
   const bool fft8 = pr.par.ntheta == 8;
   if (fft8) {
     pie_status s = fft_prepare<8, Rf>();
@@ -952,10 +1044,10 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
         static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l));
   }
   for (int l = L - 1; l >= 3 && !fft8; --l) {
-    k_interp<Rf><<<dim3(nblk(pr.lev[l].nb, fbp), nr), dim3(tpb, fbp), sm * fbp, st>>>(
+    k_interp<Rf><<<dim3(nblk(pr.lev[l].nb, fbp), nr), dim3(tpb, fbp), fsm_bytes + sm * fbp * cg, st>>>(
         P, pr.lev[l].nb, pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
         static_cast<const Rf*>(pr.lev[l].Ft), static_cast<const C2<Rf>*>(pr.lev[l].phase),
-        static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l));
+        static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l), cg, fsh);
   }
   prof_mark(pr, 3, true, st);
   prof_mark(pr, 4, false, st);
@@ -979,10 +1071,10 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
         static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1));
   }
   for (int l = 3; l < L && !fft8; ++l) {
-    k_anterp<Rf><<<dim3(nblk(pr.lev[l + 1].nb, fbp), nr), dim3(tpb, fbp), sm * fbp, st>>>(
+    k_anterp<Rf><<<dim3(nblk(pr.lev[l + 1].nb, fbp), nr), dim3(tpb, fbp), fsm_bytes + sm * fbp, st>>>(
         P, pr.lev[l + 1].nb, pr.lev[l + 1].parent, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
         static_cast<const Rf*>(pr.lev[l].F), static_cast<const C2<Rf>*>(pr.lev[l].phase),
-        static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1));
+        static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1), fsh);
   }
   prof_mark(pr, 5, true, st);
   prof_mark(pr, 6, false, st);

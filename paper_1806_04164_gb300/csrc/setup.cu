@@ -793,18 +793,29 @@ __global__ void k_plane_absmax(int64_t nnz, const cf* __restrict__ mom, unsigned
 }
 
 // out = round-to-nearest half of (value * 2^e[plane]), plane by plane.
+// One thread per pair: the eight planes' entries e become the pair's record
+// of eight half pairs (32 bytes, entry-major [nnz][8]).
 __global__ void k_to_half(int64_t nnz, const cf* __restrict__ mom, MomScale mul, __half2* __restrict__ out) {
-  const int q = blockIdx.y;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += int64_t(gridDim.x) * blockDim.x) {
-    const cf v = mom[q * nnz + e];
-    out[q * nnz + e] = __floats2half2_rn(v.x * mul.s[q], v.y * mul.s[q]);
+    uint32_t w[kMom];
+#pragma unroll
+    for (int q = 0; q < kMom; ++q) {
+      const cf v = mom[q * nnz + e];
+      const __half2 h = __floats2half2_rn(v.x * mul.s[q], v.y * mul.s[q]);
+      memcpy(&w[q], &h, sizeof(h));
+    }
+    uint4* o = reinterpret_cast<uint4*>(out + kMom * e);
+    o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    o[1] = make_uint4(w[4], w[5], w[6], w[7]);
   }
 }
 
 // PIE_FP32H: the float moments built by setup_t become half pairs, each
 // plane scaled by the power of two that puts its largest magnitude in
 // [2^14, 2^15) (half's largest finite value is 65504); the scale's inverse is
-// kept in pr.mom_scale.  The float planes are freed.
+// kept in pr.mom_scale.  The half moments are stored pair by pair ([nnz][8],
+// one 32-byte record per pair, read with two 16-byte loads), unlike the
+// plane-major float and double moments.  The float planes are freed.
 static pie_status moments_to_half(Problem& pr, cudaStream_t st) {
   pie_status s = PIE_OK;
   const int64_t nnz = pr.nnz;
@@ -829,7 +840,7 @@ static pie_status moments_to_half(Problem& pr, cudaStream_t st) {
     mul.s[q] = std::ldexp(1.0f, sh);
     pr.mom_scale[q] = std::ldexp(1.0f, -sh);
   }
-  k_to_half<<<dim3(std::max(grid, 1u), kMom), 256, 0, st>>>(nnz, mom, mul, h);
+  k_to_half<<<std::max(grid, 1u), 256, 0, st>>>(nnz, mom, mul, h);
   if ((s = cuda_check(cudaStreamSynchronize(st), "moments to half")) != PIE_OK) return s;
   // release the float planes and the range buffer
   auto release = [&](void* ptr, size_t bytes) {

@@ -124,15 +124,17 @@ __global__ void k_axs(int64_t N, double alpha, const C2<B>* __restrict__ x, C2<B
 // each warp runs it against its share of a chunk of kDotVecs vectors, every
 // lane streaming kDotTile / 32 entries of a vector before one warp
 // reduction; grid = (tiles, vector chunks).
-constexpr int kTile = 2048;
+constexpr int kTile = 2048;     // largest tile (entries of w per block)
+constexpr int kMinTile = 256;   // smallest, for short vectors
 constexpr int kDotVecs = 64;
 template <typename B>
 __global__ void __launch_bounds__(kRedThreads) k_mdot(int64_t N, int nv, const C2<B>* __restrict__ V, int64_t ldv,
-                                                      const C2<B>* __restrict__ w, cd* __restrict__ partial) {
+                                                      const C2<B>* __restrict__ w, cd* __restrict__ partial,
+                                                      int tile) {
   __shared__ C2<B> ws[kTile];
-  const int64_t n0 = int64_t(blockIdx.x) * kTile;
-  const int lim = int(min(int64_t(kTile), N - n0));
-  for (int k = threadIdx.x; k < kTile; k += kRedThreads) ws[k] = k < lim ? w[n0 + k] : mk<B>(0, 0);
+  const int64_t n0 = int64_t(blockIdx.x) * tile;
+  const int lim = int(min(int64_t(tile), N - n0));
+  for (int k = threadIdx.x; k < tile; k += kRedThreads) ws[k] = k < lim ? w[n0 + k] : mk<B>(0, 0);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c = warp; c < kDotVecs; c += kRedThreads / 32) {
@@ -394,9 +396,15 @@ struct EventPair {
 // conj(a) . b over N entries, deterministic; result on the host.
 template <typename B>
 static pie_status dotc(Ctx& c, int nv, const C2<B>* V, const C2<B>* w, zc* out_host) {
-  const unsigned tiles = unsigned((c.N + kTile - 1) / kTile);
+  // tiles of kTile entries, smaller (down to kMinTile) when that leaves fewer
+  // than two blocks per SM
+  int tile = kTile;
+  if ((c.N + kTile - 1) / kTile < 2 * int64_t(c.pr.nsm))
+    tile = int(std::max<int64_t>(kMinTile, ((c.N / (2 * std::max(c.pr.nsm, 1)) + 31) / 32) * 32));
+  tile = std::min(tile, kTile);
+  const unsigned tiles = unsigned((c.N + tile - 1) / tile);
   k_mdot<B><<<dim3(tiles, unsigned((nv + kDotVecs - 1) / kDotVecs)), kRedThreads, 0, c.st>>>(c.N, nv, V, c.N, w,
-                                                                                            c.partial);
+                                                                                            c.partial, tile);
   k_mdot_finish<<<nb_(int64_t(nv) * 32, 128), 128, 0, c.st>>>(nv, int(tiles), c.partial, c.hdev);
   pie_status s = cuda_check(cudaMemcpyAsync(out_host, c.hdev, sizeof(cd) * nv, cudaMemcpyDeviceToHost, c.st), "dot");
   if (s == PIE_OK) s = cuda_check(cudaStreamSynchronize(c.st), "dot sync");
@@ -609,7 +617,7 @@ static pie_status solve_t(Problem& pr, int op, const void* bv, void* xv, double 
   cd* u = wk.get<cd>(N, s);
   cd* wd = wk.get<cd>(N, s);
   cd* r = wk.get<cd>(N, s);
-  cd* partial = wk.get<cd>(std::max(size_t((N + kTile - 1) / kTile) * (m + 2), size_t(nb_(N, kRedThreads))), s);
+  cd* partial = wk.get<cd>(std::max(size_t((N + kMinTile - 1) / kMinTile) * (m + 2), size_t(nb_(N, kRedThreads))), s);
   cd* hdev = wk.get<cd>(m + 3, s);
   if (s != PIE_OK) return s;
   EventPair evp;
@@ -767,7 +775,8 @@ static pie_status nested_t(Problem& po, Problem& pi, const cd* b, cd* x, const p
   cd* r = wk.get<cd>(N, s);
   cf* u32 = pi.io_f32() ? wk.get<cf>(N, s) : nullptr;
   cf* w32 = pi.io_f32() ? wk.get<cf>(N, s) : nullptr;
-  cd* partial = wk.get<cd>(std::max(size_t((N + kTile - 1) / kTile) * (mmax + 2), size_t(nb_(N, kRedThreads))), s);
+  cd* partial = wk.get<cd>(std::max(size_t((N + kMinTile - 1) / kMinTile) * (mmax + 2), size_t(nb_(N, kRedThreads))),
+                           s);
   cd* hdev = wk.get<cd>(mmax + 3, s);
   if (s != PIE_OK) return s;
   EventPair evo, evi;
