@@ -42,7 +42,11 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_BYTES_PER_FLOP = {"translation": 78.880256e6 / 1.33758976e9}
 # inner operator of the nested solve and its settings
 INNER = dict(tau=3, kappa_a=0.15, ntheta=4)
+# (short inner cycles: fastest at 819,200 unknowns, kR = 1e-3, over 6 plane
+# waves; the 3,276,800-unknown sphere at kR = 1e-4 needs the stronger inner
+# solves of NESTED_LARGE to get past the far part's rounding floor near 1e-6)
 NESTED = dict(inner_restart=10, inner_tol=0.1, outer_restart=80, max_outer=1000, maxit=12000)
+NESTED_LARGE = dict(inner_restart=20, inner_tol=0.05, outer_restart=80, max_outer=1500, maxit=30000)
 
 
 def parse():
@@ -396,6 +400,23 @@ def run_ours(args):
     line["gmres"] = main["gmres"]
     line["gmres_nested"] = main["nested"]
     line["large_nested"] = results.get("large")
+    # one short record of the headline figures, last, so that it survives
+    # wherever the line is cut
+    def pick(d, *keys):
+        for k in keys:
+            d = d.get(k) if isinstance(d, dict) else None
+        return d
+    line["summary"] = {
+        "matvecs_per_s_mixed": line["value"], "matvecs_per_s_mixed_e2e": line["e2e"]["value"],
+        "matvecs_per_s_fp64": line["fp64"]["value"], "matvecs_per_s_fp64_e2e": line["fp64"]["e2e_value"],
+        "matvecs_per_s_mixed_batched8": pick(line, "batched8", "value"),
+        "matvecs_per_s_inner_fp32h": pick(line, "inner_fp32h", "matvecs_per_s"),
+        "roofline_frac": roof["frac"], "roofline_kernel": roof["kernel"],
+        "gmres_1e6_s_nested": pick(line, "gmres_nested", "seconds"),
+        "gmres_1e6_s_nested_mean_4_waves": pick(line, "gmres_nested", "seconds_mean_4_waves"),
+        "gmres_1e6_s_mixed": pick(line, "gmres", "seconds"), "gmres_1e6_s_fp64": pick(line, "gmres_fp64", "seconds"),
+        "gmres_1e6_s_nested_3M": pick(line, "large_nested", "seconds"),
+        "cpu_oracle_matvecs_per_s": pick(line, "cpu_baseline", "value")}
     print(json.dumps(line))
 
 
@@ -478,7 +499,7 @@ def multimesh_run(args, stream, barrier, max_over_ranks):
 def large_nested_run(args, barrier, max_over_ranks):
     """The large sphere (icosphere n = 8: 1,310,720 triangles, N = 3,276,800,
     kR = 1e-4, 8 levels): nested solve to 1e-6 (MIXED outer operator,
-    PIE_FP32H inner operator at INNER, settings NESTED) for the x-polarised
+    PIE_FP32H inner operator at INNER, settings NESTED_LARGE) for the x-polarised
     plane wave along -z, and the E-plane RCS of the solution against the
     Rayleigh limit.  Set-up untimed and reported; plain GMRES on this sphere
     runs under --workload large."""
@@ -498,14 +519,14 @@ def large_nested_run(args, barrier, max_over_ranks):
     b = po.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
     torch.cuda.synchronize()
     barrier()
-    x, st = po.solve_nested(b, pin, tol=args.gmres_tol, **NESTED)
+    x, st = po.solve_nested(b, pin, tol=args.gmres_tol, **NESTED_LARGE)
     barrier()
     out = {"workload": "pec_sphere_icosphere8_3M", "N": po.N, "kR": k0, "levels": L, "tol": args.gmres_tol,
            "seconds": max_over_ranks(st["seconds"]), "converged": st["converged"], "rel_residual": st["rel_residual"],
            "inner_iterations": st["inner_iterations"], "outer_products": st["outer_products"],
            "inner_product_seconds": st["inner_product_seconds"], "outer_product_seconds": st["outer_product_seconds"],
            "rcs_max_db_err_vs_rayleigh": rcs_err_db(po, x, k0), "setup_s_both": setup_s,
-           "device_bytes": po.device_bytes + pin.device_bytes}
+           "device_bytes": po.device_bytes + pin.device_bytes, "settings": dict(NESTED_LARGE)}
     del po, pin, x, b
     torch.cuda.empty_cache()
     return out
@@ -562,7 +583,7 @@ def run_large(args):
             pin = pg.Problem(mesh, k0, L, root_side=2.0, precision=pg.PIE_FP32H, **INNER)
             pin.autotune(nrhs=1, reps=3)
             b = pr.rhs_planewave([0, 0, -1.0], [1.0, 0, 0])
-            xs, st = pr.solve_nested(b, pin, tol=args.gmres_tol, **NESTED)
+            xs, st = pr.solve_nested(b, pin, tol=args.gmres_tol, **NESTED_LARGE)
             res["gmres_nested"] = {"seconds": st["seconds"], "converged": st["converged"],
                                    "inner_iterations": st["inner_iterations"],
                                    "outer_products": st["outer_products"],
@@ -623,12 +644,14 @@ def nested_run(pg, mesh, nlev, po, x_host, tol, k0, barrier, max_over_ranks, no_
     the plane wave along -z, x-polarised: flexible GMRES on po, each outer
     step preconditioned by one GMRES cycle on the complex-float PIE_FP32H
     operator at INNER (set-up and autotuning untimed).  Also the inner
-    operator's product time and the HBM roofline of its near kernel."""
+    operator's product time (1 and 8 right-hand sides per pass) and the HBM
+    roofline of its near kernel."""
+    import numpy as np
     import torch
 
     import pie_inputs as pi
     stream = torch.cuda.current_stream()
-    pin = pg.Problem(mesh, k0, nlev, root_side=2.0, precision=pg.PIE_FP32H, **INNER)
+    pin = pg.Problem(mesh, k0, nlev, root_side=2.0, precision=pg.PIE_FP32H, max_nrhs=8, **INNER)
     if not no_autotune:
         pin.autotune(nrhs=1, reps=5)
     x = torch.from_numpy(x_host).to(torch.complex64).cuda()
@@ -649,10 +672,25 @@ def nested_run(pg, mesh, nlev, po, x_host, tol, k0, barrier, max_over_ranks, no_
         pin.apply(x, y)
     stage_ms, na = pin.profile_end()
     near_ms = stage_ms["near"] / max(1, na)
+    # 8 right-hand sides per pass: each pair's half moments are read once for
+    # all 8 columns (the near part is HBM-bound, so the batch pays here)
+    x8 = torch.from_numpy(np.stack([pi.complex_normal(pin.N, 77 + j) for j in range(8)])).to(torch.complex64).cuda()
+    y8 = torch.empty_like(x8)
+    for _ in range(3):
+        pin.apply(x8, y8)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        pin.apply(x8, y8)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms8 = e0.elapsed_time(e1) / reps
+    del x8, y8
     near_bytes = pin.near_pairs * 32 + pin.T * 6 * 8 * 2   # half moments once, float coefficients in, potentials out
     hbm, hbm_src = peaks()
     inner = {"point": dict(INNER), "precision": "fp32h", "ms_per_product": ms, "matvecs_per_s": 1e3 / ms,
              "stage_ms": {k: round(v / max(1, na), 4) for k, v in stage_ms.items()},
+             "batched8": {"value": 8e3 / ms8, "unit": "matvecs/s", "ms_per_batch": ms8, "nrhs": 8},
              "near_roofline": {"bound": "hbm", "achieved": near_bytes / (near_ms * 1e-3) / 1e9, "peak": hbm,
                                "unit": "GB/s", "frac": near_bytes / (near_ms * 1e-3) / 1e9 / hbm,
                                "peak_source": hbm_src, "algorithmic_bytes": near_bytes},
@@ -700,10 +738,13 @@ out["mlfma_setup_s"] = time.time() - t0
 x = pi.complex_normal(M.top.N, 1234)
 M.apply(x)
 ts = []
+c0, w0 = time.process_time(), time.time()
 for _ in range(3):
     t0 = time.time()
     M.apply(x)
     ts.append(time.time() - t0)
+# threads the products kept busy on average: process CPU time over wall time
+out["mlfma_threads"] = (time.process_time() - c0) / max(time.time() - w0, 1e-9)
 out["mlfma_mvm_s"] = float(np.median(ts))
 out["mlfma_N"] = int(M.top.N)
 # dense Galerkin rows of the 819,200-unknown sphere itself
@@ -740,10 +781,12 @@ top = M.top
 x = pi.complex_normal(top.N, 1234)
 M.apply(x)
 ts = []
+c0, w0 = time.process_time(), time.time()
 for _ in range(3):
     t0 = time.time()
     M.apply(x)
     ts.append(time.time() - t0)
+out["mvm_threads_1280"] = (time.process_time() - c0) / max(time.time() - w0, 1e-9)
 out["mvm_s_1280"] = float(np.median(ts))
 # |Z_ii|^(-1/2) from the pairs of equal or edge-adjacent triangles, the
 # scaling the GPU solver applies
@@ -761,9 +804,10 @@ nprod = [0]
 def op(v):
     nprod[0] += 1
     return D * M.apply(D * v)
-t0 = time.time()
+t0, c0 = time.time(), time.process_time()
 y, its, hist = gmres(op, D * b, tol=1e-6, restart=100, maxit=1500)
 out["gmres_s_1280"] = time.time() - t0
+out["gmres_threads_1280"] = (time.process_time() - c0) / max(out["gmres_s_1280"], 1e-9)
 out["gmres_iterations_1280"] = int(its)
 out["gmres_products_1280"] = nprod[0]
 xs = D * y
@@ -777,9 +821,10 @@ if BIG:
     M = MLFMA(xyz, tri, 1e-3, 6, side=2.0)
     out["setup_s_81920"] = time.time() - t0
     x = pi.complex_normal(M.top.N, 1234)
-    t0 = time.time()
+    t0, c0 = time.time(), time.process_time()
     M.apply(x)
     out["mvm_s_81920"] = time.time() - t0
+    out["mvm_threads_81920"] = (time.process_time() - c0) / max(out["mvm_s_81920"], 1e-9)
     out["N_81920"] = int(M.top.N)
 print(json.dumps(out))
 """
@@ -803,7 +848,7 @@ def run_cpu_oracle(args):
         print(json.dumps({"workload": "cpu_oracle", "error": (out.stderr.strip().splitlines() or ["failed"])[-1]}))
         return
     d = json.loads(out.stdout.strip().splitlines()[-1])
-    print(json.dumps({"workload": "cpu_oracle", "kind": "oracle MLFMA (numpy FP64)", "cores": ncpu,
+    print(json.dumps({"workload": "cpu_oracle", "kind": "oracle MLFMA (numpy FP64)", "cores_available": ncpu,
                       "cpu_model": cpu_model(), **d}))
 
 
@@ -838,7 +883,8 @@ def cpu_baseline(nrows):
     d = json.loads(out.stdout.strip().splitlines()[-1])
     scale = (WORKLOAD["N"] * (WORKLOAD["levels"] - 2)) / (d["mlfma_N"] * 1)
     value = 1.0 / (d["mlfma_mvm_s"] * scale)
-    return {"value": value, "unit": "matvecs/s", "cores": ncpu, "cpu_model": cpu_model(), "kind": "oracle MLFMA",
+    return {"value": value, "unit": "matvecs/s", "cores": max(1, round(d["mlfma_threads"])), "cores_available": ncpu,
+            "threads_busy_avg": d["mlfma_threads"], "cpu_model": cpu_model(), "kind": "oracle MLFMA",
             "sample": (f"oracle MLFMA (numpy FP64) products on the 1280-triangle sphere (N = {d['mlfma_N']}, L = 3, "
                        f"one translation level): {d['mlfma_mvm_s']:.3f} s per product after a "
                        f"{d['mlfma_setup_s']:.1f} s set-up; matvecs/s at N = 819,200, 5 translation levels = "

@@ -414,14 +414,28 @@ pie_status pie_nearfield(pie_problem* pr, const void* x, const void* rho, const 
  *    carries (each pair's moments are read once for them): 1, 2, 4 or 8, or
  *    0 to pick by the pass width (1 for one column, 2 for two or a complex
  *    double near part, 4 up to four, else 8).
+ *  far_rows: tile shape of the per-box far kernels of angular grids other
+ *    than N_theta = 8 (aggregation, dense interpolation and anterpolation,
+ *    translation; one thread per sample): boxes per block, 1, 2, 4, 8, 16 or
+ *    32, reduced where a block would exceed 1024 threads or 48 KB of shared
+ *    memory; 0 = automatic (enough boxes to fill 128 threads).
+ *  near_kernel: near-part kernel for one column with a float near part:
+ *    0 = automatic (the box-staged kernel: one block per leaf box, the box's
+ *    source coefficients in shared memory), 1 = one warp per test triangle
+ *    reading the coefficients from global memory, 2 = box-staged.  Both
+ *    take the same operations in the same order.  Other cases always use
+ *    the warp-per-triangle kernel.
  * Defaults at pie_problem_create: overlap 1, near_ctas_per_sm 2, rhs_chunk
- * max_nrhs, near_rhs_block 0.  Per-stage profiling (pie_profile_begin) runs
- * the stages in order whatever overlap says. */
+ * max_nrhs, near_rhs_block 0, far_rows 0, near_kernel 0.  Per-stage
+ * profiling (pie_profile_begin) runs the stages in order whatever overlap
+ * says. */
 typedef struct pie_tuning {
   int32_t overlap;
   int32_t near_ctas_per_sm;
   int32_t rhs_chunk;
   int32_t near_rhs_block;
+  int32_t far_rows;
+  int32_t near_kernel;
 } pie_tuning;
 
 pie_status pie_problem_get_tuning(const pie_problem* pr, pie_tuning* t);
@@ -432,11 +446,13 @@ pie_status pie_problem_set_tuning(pie_problem* pr, const pie_tuning* t);
  * scratch, contents irrelevant to the timing) under each candidate setting
  * -- overlap off, overlap with near_ctas_per_sm in {1, 2, 3, 4, 6, 8, 0},
  * rhs_chunk in the powers of two up to min(nrhs, max_nrhs), near_rhs_block
- * in {1, 2, 4, 8} up to the chosen chunk -- by CUDA events on the stream,
- * median of reps (1..100) after one warm-up each, keeps the fastest, and
- * returns it (best, host) with its milliseconds per right-hand side
- * (best_ms, host, may be NULL).  The search is greedy: the overlap grid at
- * the largest rhs_chunk first, then rhs_chunk, then near_rhs_block.  Allocates
+ * in {1, 2, 4, 8} up to the chosen chunk, far_rows in {1, 2, 4, 8, 16} when
+ * N_theta is not 8, near_kernel 1 when the chunk is one column of a float
+ * near part -- by CUDA events on the stream, median of reps (1..100) after
+ * one warm-up each, keeps the fastest, and returns it (best, host) with its
+ * milliseconds per right-hand side (best_ms, host, may be NULL).  The search
+ * is greedy: the overlap grid at the largest rhs_chunk first, then
+ * rhs_chunk, then near_rhs_block, then far_rows, then near_kernel.  Allocates
  * 2 x nrhs x N complex of scratch for its duration; synchronises the stream.
  * Errors: PIE_ERR_PARAM, PIE_ERR_OOM, PIE_ERR_CUDA. */
 pie_status pie_problem_autotune(pie_problem* pr, int nrhs, int reps, pie_tuning* best, double* best_ms,

@@ -45,11 +45,11 @@ class Info(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("overlap", ctypes.c_int32), ("near_ctas_per_sm", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
-                ("near_rhs_block", ctypes.c_int32)]
+                ("near_rhs_block", ctypes.c_int32), ("far_rows", ctypes.c_int32), ("near_kernel", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(overlap=self.overlap, near_ctas_per_sm=self.near_ctas_per_sm, rhs_chunk=self.rhs_chunk,
-                    near_rhs_block=self.near_rhs_block)
+                    near_rhs_block=self.near_rhs_block, far_rows=self.far_rows, near_kernel=self.near_kernel)
 
 
 class NestedParams(ctypes.Structure):
@@ -441,7 +441,7 @@ class Problem:
                       product_seconds=s.product_seconds) for s in st[:nrhs]]
         return (x, stats[0]) if b.dim() == 1 else (x, stats)
 
-    def solve_nested(self, b, inner, tol=1e-6, maxit=20000, inner_restart=10, inner_tol=0.1, outer_restart=80,
+    def solve_nested(self, b, inner, tol=1e-6, maxit=30000, inner_restart=20, inner_tol=0.05, outer_restart=80,
                      max_outer=1000, stream=None):
         """Nested mixed-precision solve (pie_solve_nested): flexible GMRES on
         this problem's operator, each outer step preconditioned by one GMRES

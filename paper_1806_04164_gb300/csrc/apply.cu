@@ -984,7 +984,7 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   if (rb == 0) rb = nrhs == 1 ? 1 : (nrhs == 2 || sizeof(Rm) == 8) ? 2 : nrhs <= 4 ? 4 : 8;
   if (!with_near)
     pot2 = nullptr;
-  else if (rb == 1 && sizeof(Rm) == 4) {
+  else if (rb == 1 && sizeof(Rm) == 4 && pr.tune.near_kernel != 1) {
     // one right-hand side per pass over the moments, float near part: a block per leaf box
     unsigned grid = unsigned(pr.nleaf);
     if (overlap && pr.tune.near_ctas_per_sm > 0)
@@ -1013,23 +1013,29 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   prof_mark(pr, 2, false, st);
   // far coefficients in the far precision (MIXED and FP64: the io buffer)
   const C2<Rf>* fcoef = reinterpret_cast<const C2<Rf>*>(coef);
+  // boxes per block of the per-box far kernels (threads: one per sample):
+  // tune.far_rows, or enough to fill 128 threads; at most 1024 threads
+  auto far_rows = [&](int threads) {
+    const int r = pr.tune.far_rows > 0 ? pr.tune.far_rows : (threads < 64 ? 128 / threads : 1);
+    return std::max(1, std::min(r, 1024 / threads));
+  };
   {
-    // half-grid threads per box; boxes per block so that small grids fill 128 threads
+    // half-grid threads per box
     const int ath = P / 2 < 32 ? P / 2 : ((P / 2 + 31) / 32) * 32;
-    const int abp = ath < 64 ? 128 / ath : 1;
+    const int abp = far_rows(ath);
     k_agg<Rf><<<dim3(nblk(pr.lev[L].nb, abp), nr), dim3(ath, abp), 0, st>>>(
         P, pr.par.ntheta, pr.lev[L].nb, pr.leaf_start, Pi, M, fcoef, Rf(kMu0), static_cast<C2<Rf>*>(pr.lev[L].S),
         sT, sl(L));
   }
   prof_mark(pr, 2, true, st);
   const size_t sm = sizeof(C2<Rf>) * kComp * P;
-  const int fbp = tpb < 128 ? 128 / tpb : 1;  // boxes per block of the dense-filter kernels
   // dense-filter kernels: the P x P filter in shared memory when it is at
-  // most 16 KB; interpolation stages up to eight children per parent within
-  // 48 KB of shared memory in all
+  // most 16 KB; boxes per block within 48 KB of shared memory; interpolation
+  // stages up to eight children per parent in what is left
   const size_t fsb = ((sizeof(Rf) * size_t(P) * P + 15) / 16) * 16;
   const bool fsh = fsb <= 16384;
   const size_t fsm_bytes = fsh ? fsb : 0;
+  const int fbp = std::max(1, std::min(far_rows(tpb), int((49152 - fsm_bytes) / sm)));
   const int cg = int(std::max<size_t>(1, std::min<size_t>(8, (49152 - fsm_bytes) / (sm * fbp))));
   const bool fft8 = pr.par.ntheta == 8;
   if (fft8) {
@@ -1057,7 +1063,7 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
       if (s != PIE_OK) return s;
       continue;
     }
-    const int tbp = tpb < 128 ? 128 / tpb : 1;  // destination boxes per block
+    const int tbp = far_rows(tpb);  // destination boxes per block
     k_trans<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp), 0, st>>>(
         P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off, static_cast<const C2<Rf>*>(pr.lev[l].trans),
         static_cast<const C2<Rf>*>(pr.lev[l].S), static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
@@ -1112,11 +1118,17 @@ static pie_status apply_near_t(Problem& pr, const void* xv, void* yv, cudaStream
   const C2<Rm>* ncoef = split ? reinterpret_cast<const C2<Rm>*>(coef32) : reinterpret_cast<const C2<Rm>*>(coef);
   k_coef<Rio><<<nblk(pr.T, 256), 256, 0, st>>>(pr.T, pr.E, static_cast<const C2<Rio>*>(xv), pr.perm, pr.tri_edge,
                                                pr.tri_c, pr.tri_dcp, pr.w * pr.w * eps0(), coef, coef32);
-  if constexpr (sizeof(Rm) == 4)
-    k_near_box<Rio, H16><<<unsigned(pr.nleaf), 256, 0, st>>>(
-        pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
-        static_cast<const cf*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, float(kMu0), pot);
-  else
+  bool boxed = false;  // the box-staged kernel (float near part, unless tuned off)
+  if constexpr (sizeof(Rm) == 4) {
+    if (pr.tune.near_kernel != 1) {
+      k_near_box<Rio, H16><<<unsigned(pr.nleaf), 256, 0, st>>>(
+          pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
+          static_cast<const cf*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, float(kMu0),
+          pot);
+      boxed = true;
+    }
+  }
+  if (!boxed)
     k_near<Rm, Rio, 1, H16><<<nblk(pr.T * 32, 256), 256, 0, st>>>(
         pr.T, pr.nnz, pr.leaf_of, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
         static_cast<const C2<Rm>*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, Rm(kMu0),

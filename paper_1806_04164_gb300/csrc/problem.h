@@ -104,7 +104,7 @@ struct Problem {
   int nsm = 0;                   // SMs of the device
   int device = 0;                // the device the problem was built on (current at pie_problem_create)
   void* noalloc_scratch = nullptr;  // device address of the fixed scratch of pie_apply_near_noalloc
-  pie_tuning tune{1, 2, 1, 0};
+  pie_tuning tune{1, 2, 1, 0, 0, 0};
   // parts of the product that run (pie_apply_levels): translations at the
   // levels whose bit is set, and the near part
   uint32_t far_mask = 0xffffffffu;

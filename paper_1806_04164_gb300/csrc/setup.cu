@@ -774,7 +774,7 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   if ((s = cuda_check(cudaStreamCreateWithFlags(&pr.side, cudaStreamNonBlocking), "side stream")) != PIE_OK) return s;
   if ((s = cuda_check(cudaEventCreateWithFlags(&pr.ev_fork, cudaEventDisableTiming), "event")) != PIE_OK) return s;
   if ((s = cuda_check(cudaEventCreateWithFlags(&pr.ev_join, cudaEventDisableTiming), "event")) != PIE_OK) return s;
-  pr.tune = pie_tuning{1, 2, pr.par.max_nrhs, 0};
+  pr.tune = pie_tuning{1, 2, pr.par.max_nrhs, 0, 0, 0};
   return cuda_check(cudaStreamSynchronize(st), "setup");
 }
 

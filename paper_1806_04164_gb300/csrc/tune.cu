@@ -17,7 +17,10 @@ bool tuning_valid(const Problem& pr, const pie_tuning& t) {
   return (t.overlap == 0 || t.overlap == 1) && t.near_ctas_per_sm >= 0 && t.near_ctas_per_sm <= 32 &&
          t.rhs_chunk >= 1 && t.rhs_chunk <= pr.par.max_nrhs &&
          (t.near_rhs_block == 0 || t.near_rhs_block == 1 || t.near_rhs_block == 2 || t.near_rhs_block == 4 ||
-          t.near_rhs_block == 8);
+          t.near_rhs_block == 8) &&
+         (t.far_rows == 0 || t.far_rows == 1 || t.far_rows == 2 || t.far_rows == 4 || t.far_rows == 8 ||
+          t.far_rows == 16 || t.far_rows == 32) &&
+         t.near_kernel >= 0 && t.near_kernel <= 2;
 }
 
 bool profiling(const Problem& pr) { return pr.prof_n < pr.prof_cap; }
@@ -68,7 +71,7 @@ pie_status autotune(Problem& pr, int nrhs, int reps, cudaStream_t st, pie_tuning
   if (s != PIE_OK) return s;
   const pie_tuning saved = pr.tune;
   const int cmax = std::min(nrhs, pr.par.max_nrhs);
-  pie_tuning win{0, 0, cmax, 0};
+  pie_tuning win{0, 0, cmax, 0, 0, 0};
   double win_ms = 1e300;
   auto trial = [&](pie_tuning t) -> pie_status {
     pr.tune = t;
@@ -81,18 +84,33 @@ pie_status autotune(Problem& pr, int nrhs, int reps, cudaStream_t st, pie_tuning
     return r;
   };
   // overlap and the near kernel's grid, at the widest chunk
-  s = trial(pie_tuning{0, 0, cmax, 0});
+  s = trial(pie_tuning{0, 0, cmax, 0, 0, 0});
   const int ctas[] = {1, 2, 3, 4, 6, 8, 0};
   for (int c : ctas)
-    if (s == PIE_OK) s = trial(pie_tuning{1, c, cmax, 0});
+    if (s == PIE_OK) s = trial(pie_tuning{1, c, cmax, 0, 0, 0});
   // then the chunk of right-hand sides per pass
   const pie_tuning lead = win;
-  for (int c = 1; c < cmax && s == PIE_OK; c *= 2) s = trial(pie_tuning{lead.overlap, lead.near_ctas_per_sm, c, 0});
+  for (int c = 1; c < cmax && s == PIE_OK; c *= 2)
+    s = trial(pie_tuning{lead.overlap, lead.near_ctas_per_sm, c, 0, 0, 0});
   // then the right-hand sides per near-kernel thread (the automatic choice
   // is the one already timed)
   const pie_tuning lead2 = win;
   for (int rb = 1; rb <= 8 && rb <= lead2.rhs_chunk && lead2.rhs_chunk > 1 && s == PIE_OK; rb *= 2)
-    s = trial(pie_tuning{lead2.overlap, lead2.near_ctas_per_sm, lead2.rhs_chunk, rb});
+    s = trial(pie_tuning{lead2.overlap, lead2.near_ctas_per_sm, lead2.rhs_chunk, rb, 0, 0});
+  // then the tile of the per-box far kernels (N_theta = 8 uses the
+  // factorised filter kernels, whose tile is fixed)
+  if (pr.par.ntheta != 8)
+    for (int rows = 1; rows <= 16 && s == PIE_OK; rows *= 2) {
+      pie_tuning t = win;
+      t.far_rows = rows;
+      s = trial(t);
+    }
+  // then the near kernel, where both apply
+  if (win.rhs_chunk == 1 && pr.near_f32() && s == PIE_OK) {
+    pie_tuning t = win;
+    t.near_kernel = 1;
+    s = trial(t);
+  }
   if (s != PIE_OK) {
     pr.tune = saved;
     return s;

@@ -37,7 +37,7 @@ int main(void) {
   p.ntheta = 7; /* odd: no antipodal grid */
   pie_problem* pr = NULL;
   if (pie_problem_create(m, 0.01, &p, NULL, &pr) != PIE_ERR_PARAM) return fail("odd ntheta accepted");
-  pie_tuning t = {1, 2, 1, 0};
+  pie_tuning t = {1, 2, 1, 0, 0, 0};
   if (pie_problem_set_tuning(NULL, &t) != PIE_ERR_PARAM) return fail("NULL problem accepted");
   if (pie_group_create(NULL, 1, NULL) != PIE_ERR_PARAM) return fail("NULL group members accepted");
   pie_mesh_destroy(m);

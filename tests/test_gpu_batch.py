@@ -25,18 +25,21 @@ def columns(n, nrhs, seed):
     return torch.from_numpy(np.stack([pi.complex_normal(n, seed + j) for j in range(nrhs)])).cuda()
 
 
-SETTINGS = [dict(overlap=0, near_ctas_per_sm=0, rhs_chunk=4, near_rhs_block=0),
-            dict(overlap=1, near_ctas_per_sm=1, rhs_chunk=4, near_rhs_block=1),
-            dict(overlap=1, near_ctas_per_sm=3, rhs_chunk=2, near_rhs_block=8),
-            dict(overlap=1, near_ctas_per_sm=0, rhs_chunk=1, near_rhs_block=2),
-            dict(overlap=0, near_ctas_per_sm=5, rhs_chunk=3, near_rhs_block=4)]
+DEFAULT = dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=1, near_rhs_block=0, far_rows=0, near_kernel=0)
+SETTINGS = [dict(DEFAULT, overlap=0, near_ctas_per_sm=0, rhs_chunk=4),
+            dict(DEFAULT, near_ctas_per_sm=1, rhs_chunk=4, near_rhs_block=1),
+            dict(DEFAULT, near_ctas_per_sm=3, rhs_chunk=2, near_rhs_block=8),
+            dict(DEFAULT, near_ctas_per_sm=0, rhs_chunk=1, near_rhs_block=2),
+            dict(DEFAULT, overlap=0, near_ctas_per_sm=5, rhs_chunk=3, near_rhs_block=4),
+            dict(DEFAULT, rhs_chunk=1, near_kernel=1),
+            dict(DEFAULT, overlap=0, rhs_chunk=1, near_kernel=2, far_rows=4)]
 
 
 @pytest.mark.parametrize("prec", [0, 2])
 def test_settings_do_not_change_the_product(pg, prec):
     import torch
     pr = pg.Problem(pg.Mesh(*pi.icosphere(3)), K, 4, root_side=2.0, precision=prec, max_nrhs=4)
-    assert pr.tuning == dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=4, near_rhs_block=0)
+    assert pr.tuning == dict(DEFAULT, rhs_chunk=4)
     X = columns(pr.N, 5, 11)
     ref = pr.apply(X)
     torch.cuda.synchronize()
@@ -49,11 +52,36 @@ def test_settings_do_not_change_the_product(pg, prec):
 def test_tuning_rejects_out_of_range(pg):
     pr = pg.Problem(pg.Mesh(*pi.icosphere(2)), K, 3, root_side=2.0, max_nrhs=2)
     for bad in (dict(overlap=2), dict(near_ctas_per_sm=-1), dict(near_ctas_per_sm=33), dict(rhs_chunk=0),
-                dict(rhs_chunk=3), dict(near_rhs_block=3), dict(near_rhs_block=16)):
+                dict(rhs_chunk=3), dict(near_rhs_block=3), dict(near_rhs_block=16), dict(far_rows=3),
+                dict(far_rows=64), dict(far_rows=-1), dict(near_kernel=3), dict(near_kernel=-1)):
         with pytest.raises(pg.PieError) as ei:
             pr.tuning = bad
         assert ei.value.code == 1
-    assert pr.tuning == dict(overlap=1, near_ctas_per_sm=2, rhs_chunk=2, near_rhs_block=0)
+    assert pr.tuning == dict(DEFAULT, rhs_chunk=2)
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_tile_settings_do_not_change_the_small_grid_product(pg, prec):
+    """At the inner operator's point (tau = 3, kappa a = 0.15, N_theta = 4,
+    P = 32) the far part runs the per-box kernels whose tile far_rows sets,
+    and one column of a float near part the kernel near_kernel picks: every
+    combination gives the default product bit for bit, for one column and
+    for a batch."""
+    import torch
+    pr = pg.Problem(pg.Mesh(*pi.icosphere(3)), K, 4, root_side=2.0, precision=prec, max_nrhs=4,
+                    tau=3, kappa_a=0.15, ntheta=4)
+    X = columns(pr.N, 3, 31).to(torch.complex64)
+    ref1 = pr.apply(X[0].contiguous())
+    ref3 = pr.apply(X)
+    torch.cuda.synchronize()
+    for rows in (1, 2, 4, 8, 16, 32):
+        for nk in (0, 1, 2):
+            for ov in (0, 1):
+                s = dict(DEFAULT, overlap=ov, rhs_chunk=1, far_rows=rows, near_kernel=nk)
+                pr.tuning = s
+                assert torch.equal(pr.apply(X[0].contiguous()), ref1), s
+        pr.tuning = dict(DEFAULT, rhs_chunk=4, far_rows=rows)
+        assert torch.equal(pr.apply(X), ref3), rows
 
 
 def test_autotune_keeps_the_product(pg):
@@ -66,6 +94,7 @@ def test_autotune_keeps_the_product(pg):
     assert best == pr.tuning
     assert best["overlap"] in (0, 1) and 0 <= best["near_ctas_per_sm"] <= 32 and 1 <= best["rhs_chunk"] <= 4
     assert best["near_rhs_block"] in (0, 1, 2, 4, 8)
+    assert best["far_rows"] in (0, 1, 2, 4, 8, 16, 32) and best["near_kernel"] in (0, 1, 2)
     assert torch.equal(pr.apply(X), ref)
 
 
