@@ -42,10 +42,11 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_BYTES_PER_FLOP = {"translation": 78.880256e6 / 1.33758976e9}
 # inner operator of the nested solve and its settings
 INNER = dict(tau=3, kappa_a=0.15, ntheta=4)
-# (short inner cycles: fastest at 819,200 unknowns, kR = 1e-3, over 6 plane
-# waves; the 3,276,800-unknown sphere at kR = 1e-4 needs the stronger inner
-# solves of NESTED_LARGE to get past the far part's rounding floor near 1e-6)
-NESTED = dict(inner_restart=10, inner_tol=0.1, outer_restart=80, max_outer=1000, maxit=12000)
+# (inner cycles of 20 steps to 0.05: shorter cycles were faster on some
+# plane waves but took 5x more outer products on others, the count turning
+# on the rounding of the far parts near the 1e-6 floor; the large sphere is
+# allowed more outer products)
+NESTED = dict(inner_restart=20, inner_tol=0.05, outer_restart=80, max_outer=1000, maxit=20000)
 NESTED_LARGE = dict(inner_restart=20, inner_tol=0.05, outer_restart=80, max_outer=1500, maxit=30000)
 
 

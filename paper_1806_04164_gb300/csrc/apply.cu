@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
 // operations, so the same result to the last bit).  Rows longer than
 // kNearStage read the coefficients from global memory instead.
 constexpr int kNearStage = 512;
+constexpr int kNearBoxThreads = 128;  // threads per block (per leaf box); 256 measured 8 % slower (FP32H)
 template <typename Rio, bool H16>
-__global__ void __launch_bounds__(256, 3) k_near_box(int64_t nleaf, int64_t nnz, const int32_t* __restrict__ leaf_start,
+__global__ void __launch_bounds__(kNearBoxThreads, 768 / kNearBoxThreads) k_near_box(int64_t nleaf, int64_t nnz, const int32_t* __restrict__ leaf_start,
                                                   const int32_t* __restrict__ near_ptr,
                                                   const int32_t* __restrict__ near_idx,
                                                   const int32_t* __restrict__ near_off,
@@ -200,14 +201,15 @@ __global__ void __launch_bounds__(256, 3) k_near_box(int64_t nleaf, int64_t nnz,
     const bool staged = len <= kNearStage;
     __syncthreads();  // the previous box's readers are done with cs
     if (staged) {
+      int qi = q0;  // j grows: the cursor only moves forward
       for (int j = threadIdx.x; j < len; j += blockDim.x) {
-        int qi = q0;
         while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
         const cf* c = coef + 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
 #pragma unroll
-        for (int k = 0; k < 6; ++k) cs[k][j] = c[k];
+        for (int k = 0; k < 6; ++k) cp_async(&cs[k][j], c + k);
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int t = t0 + warp; t < t1; t += nwarp) {
       const int64_t e0 = row_ptr[t];
@@ -323,23 +325,47 @@ __global__ void k_agg(int P, int ntheta, int64_t nb, const int32_t* __restrict__
     C2<Rf> A[kComp], B[kComp];
 #pragma unroll
     for (int c = 0; c < kComp; ++c) A[c] = B[c] = mk<Rf>(0, 0);
-    for (int t = t0; t < t1; ++t) {
+    // triangle t's coefficients and table entries, then its multiply-adds;
+    // in float two triangles' loads are issued together (latency-bound
+    // small grids), the multiply-adds still in triangle order
+    constexpr int U = sizeof(Rf) == 4 ? 2 : 1;
+    struct Tri {
+      C2<Rf> c[6], pi, m[3];
+    };
+    auto load = [&](int t, Tri& r) {
       const C2<Rf>* cf_ = coef + 6 * (int64_t)t;
-      C2<Rf> a = cf_[0];
-      C2<Rf> pi = Pi[(int64_t)t * Ph + q];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) r.c[k] = cf_[k];
+      r.pi = Pi[(int64_t)t * Ph + q];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) r.m[d] = M[((int64_t)t * 3 + d) * Ph + q];
+    };
+    auto accumulate = [&](const Tri& r) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        C2<Rf> m = M[((int64_t)t * 3 + d) * Ph + q];
-        C2<Rf> be = cf_[1 + d];
-        rfma(A[d], m.x, a);
-        rfma(A[d], pi.x, be);
-        rfma(B[d], m.y, a);
-        rfma(B[d], pi.y, be);
+        rfma(A[d], r.m[d].x, r.c[0]);
+        rfma(A[d], r.pi.x, r.c[1 + d]);
+        rfma(B[d], r.m[d].y, r.c[0]);
+        rfma(B[d], r.pi.y, r.c[1 + d]);
       }
-      rfma(A[3], pi.x, cf_[4]);
-      rfma(B[3], pi.y, cf_[4]);
-      rfma(A[4], pi.x, cf_[5]);
-      rfma(B[4], pi.y, cf_[5]);
+      rfma(A[3], r.pi.x, r.c[4]);
+      rfma(B[3], r.pi.y, r.c[4]);
+      rfma(A[4], r.pi.x, r.c[5]);
+      rfma(B[4], r.pi.y, r.c[5]);
+    };
+    int t = t0;
+    if constexpr (U > 1)
+      for (; t + U <= t1; t += U) {
+        Tri r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load(t + u, r[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) accumulate(r[u]);
+      }
+    for (; t < t1; ++t) {
+      Tri r;
+      load(t, r);
+      accumulate(r);
     }
     const int qa = antipode(q, ntheta);
     C2<Rf>* o = S + (int64_t)b * kComp * P;
@@ -372,8 +398,9 @@ __global__ void k_interp(int P, int64_t nb, const int32_t* __restrict__ child_st
   const size_t fbytes = fs ? ((sizeof(Rf) * P * P + 15) / 16) * 16 : 0;
   C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw + fbytes) + threadIdx.y * cg * kComp * P;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  if (fs)
-    for (int i = tid; i < P * P; i += nth) fsm[i] = Ft[i];
+  if (fs)  // P x P reals as 8-byte words (P = 2 N_theta^2 is even)
+    for (int i = tid; i < P * P * int(sizeof(Rf)) / 8; i += nth)
+      cp_async(reinterpret_cast<uint2*>(fsm) + i, reinterpret_cast<const uint2*>(Ft) + i);
   const Rf* F = fs ? fsm : Ft;
   const int64_t b = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
   const bool live = b < nb;
@@ -384,9 +411,13 @@ __global__ void k_interp(int P, int64_t nb, const int32_t* __restrict__ child_st
   for (int c = 0; c < kComp; ++c) acc[c] = mk<Rf>(0, 0);
   for (int k0 = c0;; k0 += cg) {
     const int nk = k0 < c1 ? min(cg, c1 - k0) : 0;
-    if (!__syncthreads_or(nk > 0)) break;  // every row of the block done
+    if (!__syncthreads_or(nk > 0)) {  // every row of the block done
+      cp_async_wait_all();            // (nothing may stay in flight at exit)
+      break;
+    }
     // the nk children are consecutive at level l+1: one contiguous copy
-    for (int i = threadIdx.x; i < nk * kComp * P; i += blockDim.x) sm[i] = Sc[(int64_t)k0 * kComp * P + i];
+    for (int i = threadIdx.x; i < nk * kComp * P; i += blockDim.x) cp_async(sm + i, Sc + (int64_t)k0 * kComp * P + i);
+    cp_async_wait_all();  // (also completes the filter's copy)
     __syncthreads();
     for (int k = 0; k < nk && p < P; ++k) {
       const C2<Rf>* sk = sm + k * kComp * P;
@@ -728,6 +759,75 @@ __global__ void k_trans(int P, int64_t nb, const int32_t* __restrict__ il_ptr, c
   }
 }
 
+// a4 for float patterns of at most 128 samples (the inner operator of the
+// nested solve): the interaction list of a box is cut into kTransSplit
+// contiguous chunks, one per threadIdx.y sub-row, walked as in k_trans (four
+// entries at a time), and the chunks' partial sums are added in chunk order
+// through shared memory.  A coarse level has few boxes and long lists, so
+// this shortens the chain of dependent loads a thread waits through.  The
+// order of operations depends on the list alone, never on the launch shape.
+constexpr int kTransSplit = 4;
+template <typename Rf>
+__global__ void k_trans_split(int P, int64_t nb, const int32_t* __restrict__ il_ptr,
+                              const int32_t* __restrict__ il_idx, const int32_t* __restrict__ il_off,
+                              const C2<Rf>* __restrict__ Tt, const C2<Rf>* __restrict__ S, C2<Rf>* __restrict__ G,
+                              int64_t sS = 0) {
+  constexpr int U = 4;
+  extern __shared__ unsigned char smem_raw[];
+  C2<Rf>* part = reinterpret_cast<C2<Rf>*>(smem_raw);  // [row][chunk][component][P]
+  const int r = threadIdx.y / kTransSplit, k = threadIdx.y % kTransSplit, p = threadIdx.x;
+  const int64_t d = int64_t(blockIdx.x) * (blockDim.y / kTransSplit) + r;
+  const bool live = d < nb && p < P;
+  S += blockIdx.y * sS;
+  G += blockIdx.y * sS;
+  C2<Rf> acc[kComp];
+#pragma unroll
+  for (int c = 0; c < kComp; ++c) acc[c] = mk<Rf>(0, 0);
+  if (live) {
+    const int j0 = il_ptr[d], len = il_ptr[d + 1] - j0;
+    const int q = (len + kTransSplit - 1) / kTransSplit;
+    const int a = j0 + min(len, k * q), b = j0 + min(len, (k + 1) * q);
+    int j = a;
+    for (; j + U <= b; j += U) {
+      C2<Rf> tv[U], sv[U][kComp];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        tv[u] = Tt[(int64_t)il_off[j + u] * P + p];
+        const C2<Rf>* src = S + (int64_t)il_idx[j + u] * kComp * P + p;
+#pragma unroll
+        for (int c = 0; c < kComp; ++c) sv[u][c] = src[c * P];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < kComp; ++c) cfma(acc[c], tv[u], sv[u][c]);
+    }
+    for (; j < b; ++j) {
+      C2<Rf> tv = Tt[(int64_t)il_off[j] * P + p];
+      const C2<Rf>* src = S + (int64_t)il_idx[j] * kComp * P + p;
+#pragma unroll
+      for (int c = 0; c < kComp; ++c) cfma(acc[c], tv, src[c * P]);
+    }
+  }
+  C2<Rf>* mine = part + ((int64_t)(r * kTransSplit + k) * kComp) * P;
+  if (p < P && k > 0)
+#pragma unroll
+    for (int c = 0; c < kComp; ++c) mine[c * P + p] = acc[c];
+  __syncthreads();
+  if (!live || k > 0) return;
+#pragma unroll
+  for (int kk = 1; kk < kTransSplit; ++kk) {
+    const C2<Rf>* o = part + ((int64_t)(r * kTransSplit + kk) * kComp) * P;
+#pragma unroll
+    for (int c = 0; c < kComp; ++c) {
+      acc[c].x += o[c * P + p].x;
+      acc[c].y += o[c * P + p].y;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kComp; ++c) G[((int64_t)d * kComp + c) * P + p] = acc[c];
+}
+
 // a5: anterpolation from level l to level l+1:
 // G_child += F^T (conj(phase_o) G_parent); one child box per threadIdx.y
 // row of a block (several rows for small angular grids).  With fs the
@@ -743,17 +843,21 @@ __global__ void k_anterp(int P, int64_t nc, const int32_t* __restrict__ parent, 
   const size_t fbytes = fs ? ((sizeof(Rf) * P * P + 15) / 16) * 16 : 0;
   C2<Rf>* sm = reinterpret_cast<C2<Rf>*>(smem_raw + fbytes) + threadIdx.y * kComp * P;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  if (fs)
-    for (int i = tid; i < P * P; i += nth) fsm[i] = Fg[i];
+  if (fs)  // P x P reals as 8-byte words (P = 2 N_theta^2 is even)
+    for (int i = tid; i < P * P * int(sizeof(Rf)) / 8; i += nth)
+      cp_async(reinterpret_cast<uint2*>(fsm) + i, reinterpret_cast<const uint2*>(Fg) + i);
   const Rf* F = fs ? fsm : Fg;
   const int64_t ch = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
   const bool live = ch < nc;
   const int par = live ? parent[ch] : 0;
   const int o = live ? oct_child[ch] : 0;
+  // the parent's pattern copied in, then turned in place by the thread
+  // that copied each entry: conj(phase_o) G_parent
+  for (int i = threadIdx.x; live && i < kComp * P; i += blockDim.x) cp_async(sm + i, Gp + (int64_t)par * kComp * P + i);
+  cp_async_wait_all();
   for (int i = threadIdx.x; live && i < kComp * P; i += blockDim.x) {
-    int q = i % P;
-    C2<Rf> g = Gp[(int64_t)par * kComp * P + i];
-    C2<Rf> ph = phase[o * P + q];
+    const int q = i % P;
+    const C2<Rf> g = sm[i], ph = phase[o * P + q];
     C2<Rf> h;
     h.x = ph.x * g.x + ph.y * g.y;   // conj(ph) * g
     h.y = ph.x * g.y - ph.y * g.x;
@@ -821,32 +925,46 @@ __global__ void __launch_bounds__(256) k_disagg(int64_t T, int P, const int32_t*
   C2<Rf> acc[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) acc[i] = mk<Rf>(0, 0);
-  for (int q = 0; q < Ph; ++q) {
-    C2<Rf> gs[kComp], gd[kComp];
+  // sample pair q's patterns and table entries, then its multiply-adds
+  // (issuing two sample pairs' loads together was measured slower at
+  // N = 819,200 in float: 0.096 against 0.085 ms)
+  struct Sample {
+    C2<Rf> gs[kComp], gd[kComp], pi, m[3];
+  };
+  auto load = [&](int q, Sample& r) {
 #pragma unroll
     for (int c = 0; c < kComp; ++c) {
-      gs[c] = GS[c * Ph + q];
-      gd[c] = GD[c * Ph + q];
+      r.gs[c] = GS[c * Ph + q];
+      r.gd[c] = GD[c * Ph + q];
     }
-    C2<Rf> pi = PiR[(int64_t)q * T + t];
+    r.pi = PiR[(int64_t)q * T + t];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r.m[d] = MR[((int64_t)d * Ph + q) * T + t];
+  };
+  auto accumulate = [&](const Sample& r) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      C2<Rf> m = MR[((int64_t)d * Ph + q) * T + t];
+      const C2<Rf> m = r.m[d];
       // U += Mr gs - i Mi gd
-      rfma(acc[0], m.x, gs[d]);
-      acc[0].x = fma(m.y, gd[d].y, acc[0].x);
-      acc[0].y = fma(-m.y, gd[d].x, acc[0].y);
+      rfma(acc[0], m.x, r.gs[d]);
+      acc[0].x = fma(m.y, r.gd[d].y, acc[0].x);
+      acc[0].y = fma(-m.y, r.gd[d].x, acc[0].y);
       // V_d += Pr gs - i Pi gd
-      rfma(acc[1 + d], pi.x, gs[d]);
-      acc[1 + d].x = fma(pi.y, gd[d].y, acc[1 + d].x);
-      acc[1 + d].y = fma(-pi.y, gd[d].x, acc[1 + d].y);
+      rfma(acc[1 + d], r.pi.x, r.gs[d]);
+      acc[1 + d].x = fma(r.pi.y, r.gd[d].y, acc[1 + d].x);
+      acc[1 + d].y = fma(-r.pi.y, r.gd[d].x, acc[1 + d].y);
     }
 #pragma unroll
     for (int c = 3; c < 5; ++c) {
-      rfma(acc[1 + c], pi.x, gs[c]);
-      acc[1 + c].x = fma(pi.y, gd[c].y, acc[1 + c].x);
-      acc[1 + c].y = fma(-pi.y, gd[c].x, acc[1 + c].y);
+      rfma(acc[1 + c], r.pi.x, r.gs[c]);
+      acc[1 + c].x = fma(r.pi.y, r.gd[c].y, acc[1 + c].x);
+      acc[1 + c].y = fma(-r.pi.y, r.gd[c].x, acc[1 + c].y);
     }
+  };
+  for (int q = 0; q < Ph; ++q) {
+    Sample r;
+    load(q, r);
+    accumulate(r);
   }
   C2<Rio>* o = pot + 6 * t;
 #pragma unroll
@@ -987,9 +1105,9 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   else if (rb == 1 && sizeof(Rm) == 4 && pr.tune.near_kernel != 1) {
     // one right-hand side per pass over the moments, float near part: a block per leaf box
     unsigned grid = unsigned(pr.nleaf);
-    if (overlap && pr.tune.near_ctas_per_sm > 0)
-      grid = std::min<unsigned>(grid, unsigned(pr.nsm * pr.tune.near_ctas_per_sm));
-    k_near_box<Rio, H16><<<dim3(grid, nr), 256, 0, sn>>>(
+    if (overlap && pr.tune.near_ctas_per_sm > 0)  // in CTAs of 256 threads per SM
+      grid = std::min<unsigned>(grid, unsigned(pr.nsm * pr.tune.near_ctas_per_sm * (256 / kNearBoxThreads)));
+    k_near_box<Rio, H16><<<dim3(grid, nr), kNearBoxThreads, 0, sn>>>(
         pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
         static_cast<const cf*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr),
         reinterpret_cast<const cf*>(ncoef), float(kMu0), pot2, sT, sT);
@@ -1063,10 +1181,20 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
       if (s != PIE_OK) return s;
       continue;
     }
-    const int tbp = far_rows(tpb);  // destination boxes per block
-    k_trans<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp), 0, st>>>(
-        P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off, static_cast<const C2<Rf>*>(pr.lev[l].trans),
-        static_cast<const C2<Rf>*>(pr.lev[l].S), static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
+    if (sizeof(Rf) == 4 && tpb <= 128) {  // float, small grid: each list cut into kTransSplit chunks
+      const int tbp = far_rows(tpb * kTransSplit);
+      k_trans_split<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp * kTransSplit),
+                          sizeof(C2<Rf>) * kComp * P * kTransSplit * tbp, st>>>(
+          P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off,
+          static_cast<const C2<Rf>*>(pr.lev[l].trans), static_cast<const C2<Rf>*>(pr.lev[l].S),
+          static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
+    } else {
+      const int tbp = far_rows(tpb);  // destination boxes per block
+      k_trans<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp), 0, st>>>(
+          P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off,
+          static_cast<const C2<Rf>*>(pr.lev[l].trans), static_cast<const C2<Rf>*>(pr.lev[l].S),
+          static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
+    }
   }
   prof_mark(pr, 4, true, st);
   prof_mark(pr, 5, false, st);
@@ -1121,7 +1249,7 @@ static pie_status apply_near_t(Problem& pr, const void* xv, void* yv, cudaStream
   bool boxed = false;  // the box-staged kernel (float near part, unless tuned off)
   if constexpr (sizeof(Rm) == 4) {
     if (pr.tune.near_kernel != 1) {
-      k_near_box<Rio, H16><<<unsigned(pr.nleaf), 256, 0, st>>>(
+      k_near_box<Rio, H16><<<unsigned(pr.nleaf), kNearBoxThreads, 0, st>>>(
           pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
           static_cast<const cf*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, float(kMu0),
           pot);

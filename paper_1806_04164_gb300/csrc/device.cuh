@@ -56,4 +56,23 @@ __device__ __forceinline__ R warp_sum(R v) {
   return v;
 }
 
+// Asynchronous copy of one 8- or 16-byte element from global to shared
+// memory (cp.async: the thread does not wait for the load, so a staging
+// loop keeps all its loads in flight).  Completed by cp_async_wait_all,
+// after which the issuing thread sees the element; other threads see it
+// after a barrier.
+template <typename T>
+__device__ __forceinline__ void cp_async(T* dst_shared, const T* src_global) {
+  static_assert(sizeof(T) == 8 || sizeof(T) == 16, "cp.async element of 8 or 16 bytes");
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst_shared));
+  if constexpr (sizeof(T) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src_global) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src_global) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 }  // namespace pie
