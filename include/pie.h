@@ -402,9 +402,12 @@ pie_status pie_nearfield(pie_problem* pr, const void* x, const void* rho, const 
 /* Launch choices of the product (the paper, one MATLAB process, has none;
  * they change where and how the stages run, never the arithmetic, so the
  * product is the same to the last bit under every setting).
- *  overlap: 1 = the near part (HBM-bound in PIE_MIXED) runs on a second
- *    stream of the problem, concurrently with the far part (FP64-ALU-bound);
- *    the two meet before the assembly.  0 = one stream, stages in order.
+ *  overlap: 1 = the near part (HBM-bound) runs on a second stream of the
+ *    problem and the far part on a third one of the device's highest
+ *    priority, both forked from the caller's stream after the local
+ *    coefficients and joined back before the assembly (the far part's short
+ *    kernels take SM slots ahead of the near part's many blocks).
+ *    0 = the caller's stream alone, stages in order.
  *  near_ctas_per_sm: grid of the near kernel when overlapped, in CTAs of 256
  *    threads per SM (each warp walks test triangles with a grid stride), so
  *    that it takes a bounded share of every SM beside the far kernels;

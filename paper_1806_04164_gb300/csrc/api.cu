@@ -93,10 +93,12 @@ static void free_profile(Problem& pr) {
 static void free_problem(Problem& pr) {
   free_profile(pr);
   if (pr.side) cudaStreamSynchronize(pr.side), cudaStreamDestroy(pr.side);
+  if (pr.far) cudaStreamSynchronize(pr.far), cudaStreamDestroy(pr.far);
   if (pr.ev_fork) cudaEventDestroy(pr.ev_fork);
   if (pr.ev_join) cudaEventDestroy(pr.ev_join);
-  pr.side = nullptr;
-  pr.ev_fork = pr.ev_join = nullptr;
+  if (pr.ev_far) cudaEventDestroy(pr.ev_far);
+  pr.side = pr.far = nullptr;
+  pr.ev_fork = pr.ev_join = pr.ev_far = nullptr;
   for (void* p : pr.allocs) cudaFree(p);
   pr.allocs.clear();
 }

@@ -1072,19 +1072,22 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
                                                          w2e, coef, coef32, sN, sT);
   prof_mark(pr, 0, true, st);
   // near part into pot2, far part into pot.  With tune.overlap the near part
-  // runs on the side stream (HBM-bound, a bounded grid) while the far part
-  // (FP64-ALU-bound) runs here; per-stage profiling keeps them in order.
+  // runs on the side stream (HBM-bound, a bounded grid) and the far part on
+  // the problem's high-priority stream, concurrently; per-stage profiling
+  // keeps them in order on the caller's stream.
   const bool profiling = pr.prof_n < pr.prof_cap;
   const bool with_near = pr.with_near;
   const bool overlap = pr.tune.overlap && !profiling && with_near;
   C2<Rio>* pot2 = static_cast<C2<Rio>*>(pr.pot2);
-  cudaStream_t sn = st;
+  cudaStream_t sn = st, sf = st;
   unsigned near_grid = nblk(pr.T * 32, 256);
   if (overlap) {
     pie_status s = cuda_check(cudaEventRecord(pr.ev_fork, st), "fork");
     if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(pr.side, pr.ev_fork, 0), "fork");
+    if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(pr.far, pr.ev_fork, 0), "fork");
     if (s != PIE_OK) return s;
     sn = pr.side;
+    sf = pr.far;
     if (pr.tune.near_ctas_per_sm > 0)
       near_grid = std::min<unsigned>(near_grid, unsigned(pr.nsm * pr.tune.near_ctas_per_sm));
   }
@@ -1141,7 +1144,7 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
     // half-grid threads per box
     const int ath = P / 2 < 32 ? P / 2 : ((P / 2 + 31) / 32) * 32;
     const int abp = far_rows(ath);
-    k_agg<Rf><<<dim3(nblk(pr.lev[L].nb, abp), nr), dim3(ath, abp), 0, st>>>(
+    k_agg<Rf><<<dim3(nblk(pr.lev[L].nb, abp), nr), dim3(ath, abp), 0, sf>>>(
         P, pr.par.ntheta, pr.lev[L].nb, pr.leaf_start, Pi, M, fcoef, Rf(kMu0), static_cast<C2<Rf>*>(pr.lev[L].S),
         sT, sl(L));
   }
@@ -1162,13 +1165,13 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   }
   prof_mark(pr, 3, false, st);
   for (int l = L - 1; l >= 3 && fft8; --l) {
-    k_interp_fft<8, Rf><<<dim3(unsigned(pr.lev[l].nb), nr), kFftBatch * kComp * 8, fft_smem<8, Rf>(true), st>>>(
+    k_interp_fft<8, Rf><<<dim3(unsigned(pr.lev[l].nb), nr), kFftBatch * kComp * 8, fft_smem<8, Rf>(true), sf>>>(
         pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
         static_cast<const Rf*>(pr.lev[l].Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase),
         static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l));
   }
   for (int l = L - 1; l >= 3 && !fft8; --l) {
-    k_interp<Rf><<<dim3(nblk(pr.lev[l].nb, fbp), nr), dim3(tpb, fbp), fsm_bytes + sm * fbp * cg, st>>>(
+    k_interp<Rf><<<dim3(nblk(pr.lev[l].nb, fbp), nr), dim3(tpb, fbp), fsm_bytes + sm * fbp * cg, sf>>>(
         P, pr.lev[l].nb, pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l + 1].S),
         static_cast<const Rf*>(pr.lev[l].Ft), static_cast<const C2<Rf>*>(pr.lev[l].phase),
         static_cast<C2<Rf>*>(pr.lev[l].S), sl(l + 1), sl(l), cg, fsh);
@@ -1177,20 +1180,20 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   prof_mark(pr, 4, false, st);
   for (int l = 3; l <= L; ++l) {
     if (!((pr.far_mask >> l) & 1u)) {  // level left out: no incoming pattern of its own
-      pie_status s = cuda_check(cudaMemsetAsync(pr.lev[l].G, 0, sizeof(C2<Rf>) * sl(l) * nr, st), "memset");
+      pie_status s = cuda_check(cudaMemsetAsync(pr.lev[l].G, 0, sizeof(C2<Rf>) * sl(l) * nr, sf), "memset");
       if (s != PIE_OK) return s;
       continue;
     }
     if (sizeof(Rf) == 4 && tpb <= 128) {  // float, small grid: each list cut into kTransSplit chunks
       const int tbp = far_rows(tpb * kTransSplit);
       k_trans_split<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp * kTransSplit),
-                          sizeof(C2<Rf>) * kComp * P * kTransSplit * tbp, st>>>(
+                          sizeof(C2<Rf>) * kComp * P * kTransSplit * tbp, sf>>>(
           P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off,
           static_cast<const C2<Rf>*>(pr.lev[l].trans), static_cast<const C2<Rf>*>(pr.lev[l].S),
           static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
     } else {
       const int tbp = far_rows(tpb);  // destination boxes per block
-      k_trans<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp), 0, st>>>(
+      k_trans<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp), 0, sf>>>(
           P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off,
           static_cast<const C2<Rf>*>(pr.lev[l].trans), static_cast<const C2<Rf>*>(pr.lev[l].S),
           static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
@@ -1199,13 +1202,13 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   prof_mark(pr, 4, true, st);
   prof_mark(pr, 5, false, st);
   for (int l = 3; l < L && fft8; ++l) {
-    k_anterp_fft<8, Rf><<<dim3(unsigned(pr.lev[l].nb), nr), kFftBatch * kComp * 8, fft_smem<8, Rf>(false), st>>>(
+    k_anterp_fft<8, Rf><<<dim3(unsigned(pr.lev[l].nb), nr), kFftBatch * kComp * 8, fft_smem<8, Rf>(false), sf>>>(
         pr.lev[l].child_start, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
         static_cast<const Rf*>(pr.lev[l].Kf), static_cast<const C2<Rf>*>(pr.lev[l].phase),
         static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1));
   }
   for (int l = 3; l < L && !fft8; ++l) {
-    k_anterp<Rf><<<dim3(nblk(pr.lev[l + 1].nb, fbp), nr), dim3(tpb, fbp), fsm_bytes + sm * fbp, st>>>(
+    k_anterp<Rf><<<dim3(nblk(pr.lev[l + 1].nb, fbp), nr), dim3(tpb, fbp), fsm_bytes + sm * fbp, sf>>>(
         P, pr.lev[l + 1].nb, pr.lev[l + 1].parent, pr.lev[l + 1].octant, static_cast<const C2<Rf>*>(pr.lev[l].G),
         static_cast<const Rf*>(pr.lev[l].F), static_cast<const C2<Rf>*>(pr.lev[l].phase),
         static_cast<C2<Rf>*>(pr.lev[l + 1].G), sl(l), sl(l + 1), fsh);
@@ -1216,16 +1219,18 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
     C2<Rf>* GS = static_cast<C2<Rf>*>(pr.gsgd);
     C2<Rf>* GD = GS + int64_t(pr.par.max_nrhs) * pr.lev[L].nb * kComp * (P / 2);
     const int64_t sH = int64_t(pr.lev[L].nb) * kComp * (P / 2);
-    k_gsgd<Rf><<<dim3(unsigned(pr.lev[L].nb), nr), 128, 0, st>>>(P, pr.par.ntheta,
+    k_gsgd<Rf><<<dim3(unsigned(pr.lev[L].nb), nr), 128, 0, sf>>>(P, pr.par.ntheta,
                                                                  static_cast<const C2<Rf>*>(pr.lev[L].G), GS, GD,
                                                                  sl(L), sH);
-    k_disagg<Rf, Rio><<<dim3(nblk(pr.T, 256), nr), 256, 0, st>>>(
+    k_disagg<Rf, Rio><<<dim3(nblk(pr.T, 256), nr), 256, 0, sf>>>(
         pr.T, P, pr.leaf_of, static_cast<const C2<Rf>*>(pr.PiR), static_cast<const C2<Rf>*>(pr.MR), GS, GD, pot, sH,
         sT);
   }
   prof_mark(pr, 6, true, st);
   if (overlap) {
-    pie_status s = cuda_check(cudaStreamWaitEvent(st, pr.ev_join, 0), "join");
+    pie_status s = cuda_check(cudaEventRecord(pr.ev_far, sf), "join");
+    if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(st, pr.ev_far, 0), "join");
+    if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(st, pr.ev_join, 0), "join");
     if (s != PIE_OK) return s;
   }
   prof_mark(pr, 7, false, st);

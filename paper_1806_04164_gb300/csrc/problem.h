@@ -97,10 +97,13 @@ struct Problem {
   void* vec2 = nullptr;          // [N] complex (io precision), single-layer scratch
   void* pot = nullptr;           // [max_nrhs][T][6] far-part potentials (near part too when pot2 is unused)
   void* pot2 = nullptr;          // [max_nrhs][T][6] near-part potentials of the full product
-  // the near part runs on `side`, concurrently with the far part on the
-  // caller's stream, when tune.overlap is set
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // when tune.overlap is set the near part runs on `side` (default
+  // priority) and the far part on `far`, a stream of the device's highest
+  // priority, both forked from and joined back into the caller's stream: the
+  // far part's short, latency-bound kernels then take SM slots ahead of the
+  // near part's many blocks instead of queueing behind them
+  cudaStream_t side = nullptr, far = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
   int nsm = 0;                   // SMs of the device
   int device = 0;                // the device the problem was built on (current at pie_problem_create)
   void* noalloc_scratch = nullptr;  // device address of the fixed scratch of pie_apply_near_noalloc

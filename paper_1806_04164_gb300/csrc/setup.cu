@@ -772,8 +772,15 @@ static pie_status setup_t(Problem& pr, cudaStream_t st) {
   if ((s = cuda_check(cudaDeviceGetAttribute(&pr.nsm, cudaDevAttrMultiProcessorCount, dev), "SM count")) != PIE_OK)
     return s;
   if ((s = cuda_check(cudaStreamCreateWithFlags(&pr.side, cudaStreamNonBlocking), "side stream")) != PIE_OK) return s;
+  int prio_low = 0, prio_high = 0;
+  if ((s = cuda_check(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high), "stream priorities")) != PIE_OK)
+    return s;
+  if ((s = cuda_check(cudaStreamCreateWithPriority(&pr.far, cudaStreamNonBlocking, prio_high), "far stream")) !=
+      PIE_OK)
+    return s;
   if ((s = cuda_check(cudaEventCreateWithFlags(&pr.ev_fork, cudaEventDisableTiming), "event")) != PIE_OK) return s;
   if ((s = cuda_check(cudaEventCreateWithFlags(&pr.ev_join, cudaEventDisableTiming), "event")) != PIE_OK) return s;
+  if ((s = cuda_check(cudaEventCreateWithFlags(&pr.ev_far, cudaEventDisableTiming), "event")) != PIE_OK) return s;
   pr.tune = pie_tuning{1, 2, pr.par.max_nrhs, 0, 0, 0};
   return cuda_check(cudaStreamSynchronize(st), "setup");
 }
