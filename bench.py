@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM read + write bytes per algorithmic flop of a stage's kernels, from one
 # ncu capture (profiles/); valid while those kernels are unchanged.
 # translation: k_trans<double>, one product at icosphere n=6 (levels 3..6),
-# 78.88 MB for 1.3376e9 flop
-NCU_BYTES_PER_FLOP = {"translation": 78.880256e6 / 1.33758976e9}
+# 74.84 MB for 1.3376e9 flop
+NCU_BYTES_PER_FLOP = {"translation": 74.844416e6 / 1.33758976e9}
 # inner operator of the nested solve and its settings
 INNER = dict(tau=3, kappa_a=0.15, ntheta=4)
 # (inner cycles of 20 steps to 0.05: shorter cycles were faster on some

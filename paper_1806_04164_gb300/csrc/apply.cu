@@ -1184,14 +1184,19 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
       if (s != PIE_OK) return s;
       continue;
     }
-    if (sizeof(Rf) == 4 && tpb <= 128) {  // float, small grid: each list cut into kTransSplit chunks
-      const int tbp = far_rows(tpb * kTransSplit);
-      k_trans_split<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp * kTransSplit),
-                          sizeof(C2<Rf>) * kComp * P * kTransSplit * tbp, sf>>>(
-          P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off,
-          static_cast<const C2<Rf>*>(pr.lev[l].trans), static_cast<const C2<Rf>*>(pr.lev[l].S),
-          static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
-    } else {
+    bool split_done = false;
+    if constexpr (sizeof(Rf) == 4) {
+      if (tpb <= 128) {  // float, small grid: each list cut into kTransSplit chunks
+        const int tbp = far_rows(tpb * kTransSplit);
+        k_trans_split<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp * kTransSplit),
+                            sizeof(C2<Rf>) * kComp * P * kTransSplit * tbp, sf>>>(
+            P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off,
+            static_cast<const C2<Rf>*>(pr.lev[l].trans), static_cast<const C2<Rf>*>(pr.lev[l].S),
+            static_cast<C2<Rf>*>(pr.lev[l].G), sl(l));
+        split_done = true;
+      }
+    }
+    if (!split_done) {
       const int tbp = far_rows(tpb);  // destination boxes per block
       k_trans<Rf><<<dim3(nblk(pr.lev[l].nb, tbp), nr), dim3(tpb, tbp), 0, sf>>>(
           P, pr.lev[l].nb, pr.lev[l].il_ptr, pr.lev[l].il_idx, pr.lev[l].il_off,
