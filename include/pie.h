@@ -404,7 +404,8 @@ pie_status pie_nearfield(pie_problem* pr, const void* x, const void* rho, const 
  * product is the same to the last bit under every setting).
  *  overlap: 1 = the near part (HBM-bound) runs on a second stream of the
  *    problem and the far part on a third one of the device's highest
- *    priority, both forked from the caller's stream after the local
+ *    priority (on the caller's stream while that stream is being captured
+ *    into a graph), forked from the caller's stream after the local
  *    coefficients and joined back before the assembly (the far part's short
  *    kernels take SM slots ahead of the near part's many blocks).
  *    0 = the caller's stream alone, stages in order.
@@ -413,21 +414,24 @@ pie_status pie_nearfield(pie_problem* pr, const void* x, const void* rho, const 
  *    that it takes a bounded share of every SM beside the far kernels;
  *    0 = one warp per test triangle.  0..32.
  *  rhs_chunk: right-hand sides per pass over the operator, 1..max_nrhs.
- *  near_rhs_block: right-hand sides that one thread of the near kernel
- *    carries (each pair's moments are read once for them): 1, 2, 4 or 8, or
- *    0 to pick by the pass width (1 for one column, 2 for two or a complex
- *    double near part, 4 up to four, else 8).
+ *  near_rhs_block: right-hand sides that one pass of the near kernel
+ *    carries (each pair's moments are read once for them): 1, 2, 4 or 8
+ *    (8 only with the warp-per-triangle kernel), or 0 to pick by the pass
+ *    width (1 for one column, 2 for two or a complex double near part, 4 up
+ *    to four, else 8).
  *  far_rows: tile shape of the per-box far kernels of angular grids other
  *    than N_theta = 8 (aggregation, dense interpolation and anterpolation,
  *    translation; one thread per sample): boxes per block, 1, 2, 4, 8, 16 or
  *    32, reduced where a block would exceed 1024 threads or 48 KB of shared
  *    memory; 0 = automatic (enough boxes to fill 128 threads).
- *  near_kernel: near-part kernel for one column with a float near part:
- *    0 = automatic (the box-staged kernel: one block per leaf box, the box's
- *    source coefficients in shared memory), 1 = one warp per test triangle
- *    reading the coefficients from global memory, 2 = box-staged.  Both
- *    take the same operations in the same order.  Other cases always use
- *    the warp-per-triangle kernel.
+ *  near_kernel: near-part kernel for a float near part: 1 = one warp per
+ *    test triangle reading the coefficients from global memory (1, 2, 4 or
+ *    8 right-hand sides per thread), 2 = box-staged (one block per leaf box
+ *    and group of up to 4 right-hand sides, the box's source coefficients
+ *    in shared memory), 0 = automatic (box-staged for passes of one column,
+ *    warp per triangle otherwise).  Both take the same operations in the
+ *    same order.  A complex double near part, and near_rhs_block 8, always
+ *    use the warp-per-triangle kernel.
  * Defaults at pie_problem_create: overlap 1, near_ctas_per_sm 2, rhs_chunk
  * max_nrhs, near_rhs_block 0, far_rows 0, near_kernel 0.  Per-stage
  * profiling (pie_profile_begin) runs the stages in order whatever overlap
@@ -450,9 +454,9 @@ pie_status pie_problem_set_tuning(pie_problem* pr, const pie_tuning* t);
  * -- overlap off, overlap with near_ctas_per_sm in {1, 2, 3, 4, 6, 8, 0},
  * rhs_chunk in the powers of two up to min(nrhs, max_nrhs), near_rhs_block
  * in {1, 2, 4, 8} up to the chosen chunk, far_rows in {1, 2, 4, 8, 16} when
- * N_theta is not 8, near_kernel 1 when the chunk is one column of a float
- * near part -- by CUDA events on the stream, median of reps (1..100) after
- * one warm-up each, keeps the fastest, and returns it (best, host) with its
+ * N_theta is not 8, near_kernel 1 and 2 for a float near part -- by CUDA events
+ * on the stream, median of reps (1..100) after one warm-up each, keeps the
+ * fastest, and returns it (best, host) with its
  * milliseconds per right-hand side (best_ms, host, may be NULL).  The search
  * is greedy: the overlap grid at the largest rhs_chunk first, then
  * rhs_chunk, then near_rhs_block, then far_rows, then near_kernel.  Allocates

@@ -171,28 +171,37 @@ __global__ void __launch_bounds__(256) k_near(int64_t T, int64_t nnz, const int3
   }
 }
 
-// a1, one right-hand side, float near part: one block per leaf box (grid
-// stride over boxes).  Every test triangle of a box runs over the same
-// source list (the concatenated source ranges of its near boxes), so the
-// block stages those sources' coefficients in shared memory once, plane by
-// plane ([6][len]), and its warps take the box's test triangles in turn,
-// lanes over the row as in k_near (lane j, j + 32, ...; the same order of
-// operations, so the same result to the last bit).  Rows longer than
-// kNearStage read the coefficients from global memory instead.
+// a1, float near part: one block per leaf box (grid stride over boxes) and
+// per group of RB right-hand sides (blockIdx.y).  Every test triangle of a
+// box runs over the same source list (the concatenated source ranges of its
+// near boxes), so the block stages those sources' coefficients in shared
+// memory once per right-hand side, plane by plane ([RB][6][len], dynamic
+// shared memory), and its warps take the box's test triangles in turn,
+// lanes over the row as in k_near (lane j, j + 32, ...): each moment is read
+// once for the RB right-hand sides, and every right-hand side sees the same
+// operations in the same order as in k_near, so the same result to the last
+// bit.  Rows longer than kNearStage read the coefficients from global
+// memory instead.
 constexpr int kNearStage = 512;
 constexpr int kNearBoxThreads = 128;  // threads per block (per leaf box); 256 measured 8 % slower (FP32H)
-template <typename Rio, bool H16>
-__global__ void __launch_bounds__(kNearBoxThreads, 768 / kNearBoxThreads) k_near_box(int64_t nleaf, int64_t nnz, const int32_t* __restrict__ leaf_start,
-                                                  const int32_t* __restrict__ near_ptr,
-                                                  const int32_t* __restrict__ near_idx,
-                                                  const int32_t* __restrict__ near_off,
-                                                  const int64_t* __restrict__ row_ptr, const cf* __restrict__ mom,
-                                                  const __half2* __restrict__ momh, MomScale msc,
-                                                  const cf* __restrict__ coef, float mu0, C2<Rio>* __restrict__ pot,
-                                                  int64_t sc = 0, int64_t sp = 0) {
-  __shared__ cf cs[6][kNearStage];
-  coef += blockIdx.y * sc;  // right-hand side blockIdx.y
-  pot += blockIdx.y * sp;
+template <int RB>
+constexpr size_t near_box_smem() {
+  return size_t(RB) * 6 * kNearStage * sizeof(cf);
+}
+template <typename Rio, bool H16, int RB>
+__global__ void __launch_bounds__(kNearBoxThreads, RB == 1 ? 6 : (RB == 2 ? 4 : 2))
+    k_near_box(int64_t nleaf, int64_t nnz, const int32_t* __restrict__ leaf_start,
+               const int32_t* __restrict__ near_ptr, const int32_t* __restrict__ near_idx,
+               const int32_t* __restrict__ near_off, const int64_t* __restrict__ row_ptr,
+               const cf* __restrict__ mom, const __half2* __restrict__ momh, MomScale msc,
+               const cf* __restrict__ coef, float mu0, C2<Rio>* __restrict__ pot, int nrhs = 1, int64_t sc = 0,
+               int64_t sp = 0) {
+  extern __shared__ __align__(16) unsigned char near_smem[];
+  cf* cs = reinterpret_cast<cf*>(near_smem);  // [RB][6][kNearStage]
+  const int r0 = blockIdx.y * RB;             // right-hand sides r0 .. r0 + nr - 1
+  const int nr = min(RB, nrhs - r0);
+  coef += r0 * sc;
+  pot += r0 * sp;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int64_t b = blockIdx.x; b < nleaf; b += gridDim.x) {
     const int q0 = near_ptr[b], q1 = near_ptr[b + 1];
@@ -204,52 +213,66 @@ __global__ void __launch_bounds__(kNearBoxThreads, 768 / kNearBoxThreads) k_near
       int qi = q0;  // j grows: the cursor only moves forward
       for (int j = threadIdx.x; j < len; j += blockDim.x) {
         while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
-        const cf* c = coef + 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
+        const int64_t src = 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
+        for (int r = 0; r < nr; ++r)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) cp_async(&cs[k][j], c + k);
+          for (int k = 0; k < 6; ++k) cp_async(&cs[(r * 6 + k) * kNearStage + j], coef + r * sc + src + k);
       }
     }
     cp_async_wait_all();
     __syncthreads();
     for (int t = t0 + warp; t < t1; t += nwarp) {
       const int64_t e0 = row_ptr[t];
-      cf acc[6];
+      cf acc[RB][6];
 #pragma unroll
-      for (int i = 0; i < 6; ++i) acc[i] = mk<float>(0, 0);
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[r][i] = mk<float>(0, 0);
       int qi = q0;
-      // entry j's six source coefficients (a cursor on the near box that
-      // holds j when they are not staged; j increases call by call)
-      auto coefs = [&](int j, cf* c) {
+      // entry j's six source coefficients of right-hand side r (a cursor on
+      // the near box that holds j when they are not staged; j never
+      // decreases from one call to the next)
+      auto coefs = [&](int r, int j, cf* c) {
         if (staged) {
 #pragma unroll
-          for (int k = 0; k < 6; ++k) c[k] = cs[k][j];
+          for (int k = 0; k < 6; ++k) c[k] = cs[(r * 6 + k) * kNearStage + j];
         } else {
           while (qi + 1 < q1 && near_off[qi + 1] <= j) ++qi;
-          const cf* src = coef + 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
+          const cf* src = coef + r * sc + 6 * (int64_t(leaf_start[near_idx[qi]]) + (j - near_off[qi]));
 #pragma unroll
           for (int k = 0; k < 6; ++k) c[k] = src[k];
         }
       };
       // m: m0, mt(3), ms(3), mts; c: a, beta(3), sigma, d
-      auto accumulate = [&](const cf* m, const cf* c) {
-        cfma(acc[0], c[0], m[7]);
-        cfma(acc[0], c[1], m[1]);
-        cfma(acc[0], c[2], m[2]);
-        cfma(acc[0], c[3], m[3]);
-        cfma(acc[1], c[0], m[4]);
-        cfma(acc[1], c[1], m[0]);
-        cfma(acc[2], c[0], m[5]);
-        cfma(acc[2], c[2], m[0]);
-        cfma(acc[3], c[0], m[6]);
-        cfma(acc[3], c[3], m[0]);
-        cfma(acc[4], c[4], m[0]);
-        cfma(acc[5], c[5], m[0]);
+      auto accumulate = [](cf* a, const cf* m, const cf* c) {
+        cfma(a[0], c[0], m[7]);
+        cfma(a[0], c[1], m[1]);
+        cfma(a[0], c[2], m[2]);
+        cfma(a[0], c[3], m[3]);
+        cfma(a[1], c[0], m[4]);
+        cfma(a[1], c[1], m[0]);
+        cfma(a[2], c[0], m[5]);
+        cfma(a[2], c[2], m[0]);
+        cfma(a[3], c[0], m[6]);
+        cfma(a[3], c[3], m[0]);
+        cfma(a[4], c[4], m[0]);
+        cfma(a[5], c[5], m[0]);
+      };
+      // one entry's moments against every right-hand side's coefficients
+      auto entry = [&](int j, const cf* m) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          if (r < nr) {
+            cf c[6];
+            coefs(r, j, c);
+            accumulate(acc[r], m, c);
+          }
       };
       if constexpr (H16) {
-        // entries j, j + 32, j + 64, j + 96: their 32-byte records loaded
-        // together (four pairs of 16-byte loads in flight per lane), then
-        // accumulated in that order, the order of the one-entry loop
-        constexpr int U = 4;
+        // entries j, j + 32, ... (U of them): their 32-byte records loaded
+        // together, then accumulated in that order, the order of the
+        // one-entry loop
+        constexpr int U = RB == 1 ? 4 : 2;
         for (int j = lane; j < len; j += 32 * U) {
           uint4 lo[U], hi[U];
 #pragma unroll
@@ -258,43 +281,57 @@ __global__ void __launch_bounds__(kNearBoxThreads, 768 / kNearBoxThreads) k_near
 #pragma unroll
           for (int u = 0; u < U; ++u)
             if (j + 32 * u < len) {
-              cf m[kMom], c[6];
+              cf m[kMom];
               unpack_half<float>(lo[u], hi[u], msc, m);
-              coefs(j + 32 * u, c);
-              accumulate(m, c);
+              entry(j + 32 * u, m);
             }
         }
       } else {
         // entries j and j + 32 loaded together (twice the loads in flight),
         // accumulated in the order j, j + 32 of the one-entry loop
-        auto load = [&](int j, cf* m, cf* c) {
-#pragma unroll
-          for (int q = 0; q < kMom; ++q) m[q] = mom[q * nnz + e0 + j];
-          coefs(j, c);
-        };
         for (int j = lane; j < len; j += 64) {
-          cf ma[kMom], ca[6], mb[kMom], cb[6];
+          cf ma[kMom], mb[kMom];
           const bool two = j + 32 < len;
-          load(j, ma, ca);
-          if (two) load(j + 32, mb, cb);
-          accumulate(ma, ca);
-          if (two) accumulate(mb, cb);
+#pragma unroll
+          for (int q = 0; q < kMom; ++q) ma[q] = mom[q * nnz + e0 + j];
+          if (two)
+#pragma unroll
+            for (int q = 0; q < kMom; ++q) mb[q] = mom[q * nnz + e0 + j + 32];
+          entry(j, ma);
+          if (two) entry(j + 32, mb);
         }
       }
 #pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        acc[i].x = warp_sum(acc[i].x);
-        acc[i].y = warp_sum(acc[i].y);
-      }
-      if (lane == 0) {
-        C2<Rio>* o = pot + 6 * int64_t(t);
+      for (int r = 0; r < RB; ++r) {
+        if (r >= nr) break;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) o[i] = mk<Rio>(Rio(mu0 * acc[i].x), Rio(mu0 * acc[i].y));
-        o[4] = cvt<Rio>(acc[4]);
-        o[5] = cvt<Rio>(acc[5]);
+        for (int i = 0; i < 6; ++i) {
+          acc[r][i].x = warp_sum(acc[r][i].x);
+          acc[r][i].y = warp_sum(acc[r][i].y);
+        }
+        if (lane == 0) {
+          C2<Rio>* o = pot + r * sp + 6 * int64_t(t);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) o[i] = mk<Rio>(Rio(mu0 * acc[r][i].x), Rio(mu0 * acc[r][i].y));
+          o[4] = cvt<Rio>(acc[r][4]);
+          o[5] = cvt<Rio>(acc[r][5]);
+        }
       }
     }
   }
+}
+
+// The RB = 4 instance takes more than the 48 KB of shared memory a kernel
+// gets without asking: raise its limit once per instance.
+template <typename Rio, bool H16, int RB>
+static pie_status near_box_prepare() {
+  static bool done = false;
+  if (done || near_box_smem<RB>() <= 49152) return PIE_OK;
+  pie_status s = cuda_check(cudaFuncSetAttribute(k_near_box<Rio, H16, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(near_box_smem<RB>())),
+                            "near smem attribute");
+  done = s == PIE_OK;
+  return s;
 }
 
 // Antipode of half-grid sample q (theta rows 0..ntheta/2-1): -khat_q is
@@ -1082,12 +1119,19 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   cudaStream_t sn = st, sf = st;
   unsigned near_grid = nblk(pr.T * 32, 256);
   if (overlap) {
-    pie_status s = cuda_check(cudaEventRecord(pr.ev_fork, st), "fork");
+    // inside a stream capture (a multi-mesh group's graph) the far part
+    // stays on the capturing stream: with every member's far part at the
+    // highest priority the members' near parts waited for all of them
+    // (group launch 131.4 -> 137.6 ms for the four configuration-3 meshes)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    pie_status s = cuda_check(cudaStreamIsCapturing(st, &cap), "capture status");
+    if (s == PIE_OK) s = cuda_check(cudaEventRecord(pr.ev_fork, st), "fork");
     if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(pr.side, pr.ev_fork, 0), "fork");
-    if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(pr.far, pr.ev_fork, 0), "fork");
+    if (s == PIE_OK && cap == cudaStreamCaptureStatusNone)
+      s = cuda_check(cudaStreamWaitEvent(pr.far, pr.ev_fork, 0), "fork");
     if (s != PIE_OK) return s;
     sn = pr.side;
-    sf = pr.far;
+    if (cap == cudaStreamCaptureStatusNone) sf = pr.far;
     if (pr.tune.near_ctas_per_sm > 0)
       near_grid = std::min<unsigned>(near_grid, unsigned(pr.nsm * pr.tune.near_ctas_per_sm));
   }
@@ -1101,19 +1145,36 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
         static_cast<const C2<Rm>*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, Rm(kMu0),
         pot2, nrhs, sT, sT);
   };
+  // float near part: the box-staged kernel (RB 1, 2 or 4) for one column,
+  // or for any pass when tune.near_kernel is 2; otherwise one warp per test
+  // triangle (RB 1, 2, 4 or 8).  The box kernel measured slower on passes of
+  // many columns of small meshes whose rows outgrow its staging buffer.
   int rb = pr.tune.near_rhs_block;
   if (rb == 0) rb = nrhs == 1 ? 1 : (nrhs == 2 || sizeof(Rm) == 8) ? 2 : nrhs <= 4 ? 4 : 8;
-  if (!with_near)
+  const bool boxed = sizeof(Rm) == 4 && (pr.tune.near_kernel == 2 || (pr.tune.near_kernel == 0 && rb == 1));
+  auto box_launch = [&](auto rbc) -> pie_status {
+    if constexpr (sizeof(Rm) == 4) {
+      constexpr int RB = decltype(rbc)::value;
+      pie_status s = near_box_prepare<Rio, H16, RB>();
+      if (s != PIE_OK) return s;
+      unsigned grid = unsigned(pr.nleaf);
+      if (overlap && pr.tune.near_ctas_per_sm > 0)  // in CTAs of 256 threads per SM
+        grid = std::min<unsigned>(grid, unsigned(pr.nsm * pr.tune.near_ctas_per_sm * (256 / kNearBoxThreads)));
+      k_near_box<Rio, H16, RB><<<dim3(grid, unsigned((nrhs + RB - 1) / RB)), kNearBoxThreads, near_box_smem<RB>(),
+                                 sn>>>(pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off,
+                                       pr.row_ptr, static_cast<const cf*>(pr.mom),
+                                       static_cast<const __half2*>(pr.mom), mom_scale(pr),
+                                       reinterpret_cast<const cf*>(ncoef), float(kMu0), pot2, nrhs, sT, sT);
+    }
+    return PIE_OK;
+  };
+  if (!with_near) {
     pot2 = nullptr;
-  else if (rb == 1 && sizeof(Rm) == 4 && pr.tune.near_kernel != 1) {
-    // one right-hand side per pass over the moments, float near part: a block per leaf box
-    unsigned grid = unsigned(pr.nleaf);
-    if (overlap && pr.tune.near_ctas_per_sm > 0)  // in CTAs of 256 threads per SM
-      grid = std::min<unsigned>(grid, unsigned(pr.nsm * pr.tune.near_ctas_per_sm * (256 / kNearBoxThreads)));
-    k_near_box<Rio, H16><<<dim3(grid, nr), kNearBoxThreads, 0, sn>>>(
-        pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
-        static_cast<const cf*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr),
-        reinterpret_cast<const cf*>(ncoef), float(kMu0), pot2, sT, sT);
+  } else if (boxed && (rb == 1 || rb == 2 || rb == 4)) {
+    pie_status s = rb == 1   ? box_launch(std::integral_constant<int, 1>())
+                   : rb == 2 ? box_launch(std::integral_constant<int, 2>())
+                             : box_launch(std::integral_constant<int, 4>());
+    if (s != PIE_OK) return s;
   } else if (rb == 1)
     near_launch(std::integral_constant<int, 1>());
   else if (rb == 2)
@@ -1233,8 +1294,11 @@ static pie_status apply_t(Problem& pr, const void* xv, void* yv, int nrhs, cudaS
   }
   prof_mark(pr, 6, true, st);
   if (overlap) {
-    pie_status s = cuda_check(cudaEventRecord(pr.ev_far, sf), "join");
-    if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(st, pr.ev_far, 0), "join");
+    pie_status s = PIE_OK;
+    if (sf != st) {
+      s = cuda_check(cudaEventRecord(pr.ev_far, sf), "join");
+      if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(st, pr.ev_far, 0), "join");
+    }
     if (s == PIE_OK) s = cuda_check(cudaStreamWaitEvent(st, pr.ev_join, 0), "join");
     if (s != PIE_OK) return s;
   }
@@ -1259,7 +1323,7 @@ static pie_status apply_near_t(Problem& pr, const void* xv, void* yv, cudaStream
   bool boxed = false;  // the box-staged kernel (float near part, unless tuned off)
   if constexpr (sizeof(Rm) == 4) {
     if (pr.tune.near_kernel != 1) {
-      k_near_box<Rio, H16><<<unsigned(pr.nleaf), kNearBoxThreads, 0, st>>>(
+      k_near_box<Rio, H16, 1><<<unsigned(pr.nleaf), kNearBoxThreads, near_box_smem<1>(), st>>>(
           pr.nleaf, pr.nnz, pr.leaf_start, pr.near_ptr, pr.near_idx, pr.near_off, pr.row_ptr,
           static_cast<const cf*>(pr.mom), static_cast<const __half2*>(pr.mom), mom_scale(pr), ncoef, float(kMu0),
           pot);

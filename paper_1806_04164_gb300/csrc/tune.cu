@@ -106,10 +106,14 @@ pie_status autotune(Problem& pr, int nrhs, int reps, cudaStream_t st, pie_tuning
       s = trial(t);
     }
   // then the near kernel, where both apply
-  if (win.rhs_chunk == 1 && pr.near_f32() && s == PIE_OK) {
-    pie_tuning t = win;
-    t.near_kernel = 1;
-    s = trial(t);
+  if (pr.near_f32() && s == PIE_OK) {
+    const pie_tuning lead3 = win;
+    for (int nk = 1; nk <= 2 && s == PIE_OK; ++nk) {
+      pie_tuning t = lead3;
+      t.near_kernel = nk;
+      if (nk == 2 && t.near_rhs_block == 8) continue;  // the box kernel carries at most 4
+      s = trial(t);
+    }
   }
   if (s != PIE_OK) {
     pr.tune = saved;

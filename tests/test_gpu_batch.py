@@ -64,9 +64,9 @@ def test_tuning_rejects_out_of_range(pg):
 def test_tile_settings_do_not_change_the_small_grid_product(pg, prec):
     """At the inner operator's point (tau = 3, kappa a = 0.15, N_theta = 4,
     P = 32) the far part runs the per-box kernels whose tile far_rows sets,
-    and one column of a float near part the kernel near_kernel picks: every
-    combination gives the default product bit for bit, for one column and
-    for a batch."""
+    and a float near part the kernel near_kernel picks (with 1 to 8
+    right-hand sides per pass over the moments): every combination gives
+    the default product bit for bit, for one column and for a batch."""
     import torch
     pr = pg.Problem(pg.Mesh(*pi.icosphere(3)), K, 4, root_side=2.0, precision=prec, max_nrhs=4,
                     tau=3, kappa_a=0.15, ntheta=4)
@@ -82,6 +82,13 @@ def test_tile_settings_do_not_change_the_small_grid_product(pg, prec):
                 assert torch.equal(pr.apply(X[0].contiguous()), ref1), s
         pr.tuning = dict(DEFAULT, rhs_chunk=4, far_rows=rows)
         assert torch.equal(pr.apply(X), ref3), rows
+    # several columns per pass: box-staged (1, 2 or 4 columns per block) or
+    # warp-per-triangle (1, 2, 4 or 8 per thread)
+    for nk in (0, 1, 2):
+        for rb in (0, 1, 2, 4, 8):
+            s = dict(DEFAULT, rhs_chunk=4, near_rhs_block=rb, near_kernel=nk)
+            pr.tuning = s
+            assert torch.equal(pr.apply(X), ref3), s
 
 
 def test_autotune_keeps_the_product(pg):
