@@ -91,6 +91,29 @@ def test_tile_settings_do_not_change_the_small_grid_product(pg, prec):
             assert torch.equal(pr.apply(X), ref3), s
 
 
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_near_kernels_agree_on_rows_longer_than_the_staging_buffer(pg, prec):
+    """A coarse tree (5120 triangles at L = 3, leaf boxes of 0.25 m: rows of
+    more than 512 source triangles) sends the box-staged near kernel down
+    its unstaged path, which reads the coefficients of every right-hand side
+    from global memory: 1, 2 and 4 columns per block must still give the
+    warp-per-triangle kernel's product bit for bit."""
+    import torch
+    pr = pg.Problem(pg.Mesh(*pi.icosphere(4)), K, 3, root_side=2.0, precision=prec, max_nrhs=4)
+    assert pr.near_pairs / pr.T > 512
+    dt = torch.complex64 if prec in (1, 3) else torch.complex128
+    X = columns(pr.N, 4, 41).to(dt)
+    pr.tuning = dict(DEFAULT, rhs_chunk=4, near_rhs_block=4, near_kernel=1)
+    ref = pr.apply(X)
+    for nk in (0, 2):
+        for rb in (1, 2, 4):
+            s = dict(DEFAULT, rhs_chunk=4, near_rhs_block=rb, near_kernel=nk)
+            pr.tuning = s
+            assert torch.equal(pr.apply(X), ref), s
+    pr.tuning = dict(DEFAULT, rhs_chunk=1, near_kernel=2)
+    assert torch.equal(pr.apply(X), ref)
+
 def test_autotune_keeps_the_product(pg):
     import torch
     pr = pg.Problem(pg.Mesh(*pi.icosphere(3)), K, 4, root_side=2.0, precision=pg.PIE_MIXED, max_nrhs=4)
