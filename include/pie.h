@@ -340,6 +340,11 @@ pie_status pie_solve_guess(pie_problem* pr, const void* b, void* x, int nrhs, do
  *   outer_restart: outer steps per restart (1..200); 0 = iterative
  *     refinement (x += D z for the preconditioned scaled residual);
  *   max_outer: bound on products with the outer operator per column.
+ * Measured on GB300 (PIE_MIXED outer, PIE_FP32H inner at tau 3, kappa_a
+ * 0.15, N_theta 4): inner_restart 20, inner_tol 0.05, outer_restart 80
+ * reach 1e-6 in 1.6-1.9 s at 819,200 unknowns and in 52 s at 3,276,800;
+ * shorter inner cycles were faster on some right-hand sides but needed up
+ * to 5 times more outer products on others.
  * An outer cycle ends when its rotated (scaled) residual or the unscaled
  * residual of its iterate (formed from the outer Krylov basis every step)
  * reaches tol, or after outer_restart steps; the FP64 true residual then
