@@ -3,6 +3,7 @@
 // translation (Eq. (5) operators), anterpolation, leaf disaggregation and
 // Galerkin assembly (Section 2).
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <type_traits>
 
@@ -322,15 +323,28 @@ __global__ void __launch_bounds__(kNearBoxThreads, RB == 1 ? 6 : (RB == 2 ? 4 : 
 }
 
 // The RB = 4 instance takes more than the 48 KB of shared memory a kernel
-// gets without asking: raise its limit once per instance.
+// gets without asking: raise its limit once per instance and device (the
+// attribute belongs to the current device's copy of the kernel).
+static bool device_done(std::atomic<uint64_t>& mask, int* bit) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    *bit = -1;
+    return false;
+  }
+  *bit = dev;
+  return (mask.load() >> dev) & 1u;
+}
+
 template <typename Rio, bool H16, int RB>
 static pie_status near_box_prepare() {
-  static bool done = false;
-  if (done || near_box_smem<RB>() <= 49152) return PIE_OK;
+  static std::atomic<uint64_t> done{0};
+  int bit = -1;
+  if (near_box_smem<RB>() <= 49152 || device_done(done, &bit)) return PIE_OK;
   pie_status s = cuda_check(cudaFuncSetAttribute(k_near_box<Rio, H16, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  int(near_box_smem<RB>())),
                             "near smem attribute");
-  done = s == PIE_OK;
+  if (s == PIE_OK && bit >= 0) done.fetch_or(uint64_t(1) << bit);
   return s;
 }
 
@@ -1077,8 +1091,9 @@ static size_t fft_smem(bool interp) {
 // Opt the factorised filter kernels into their (above 48 KB) dynamic shared memory.
 template <int NT, typename Rf>
 static pie_status fft_prepare() {
-  static bool done = false;
-  if (done) return PIE_OK;
+  static std::atomic<uint64_t> done{0};  // per device, as near_box_prepare
+  int bit = -1;
+  if (device_done(done, &bit)) return PIE_OK;
   pie_status s = cuda_check(cudaFuncSetAttribute(k_interp_fft<NT, Rf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  int(fft_smem<NT, Rf>(true))),
                             "smem attribute");
@@ -1086,7 +1101,7 @@ static pie_status fft_prepare() {
     s = cuda_check(cudaFuncSetAttribute(k_anterp_fft<NT, Rf>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         int(fft_smem<NT, Rf>(false))),
                    "smem attribute");
-  done = s == PIE_OK;
+  if (s == PIE_OK && bit >= 0) done.fetch_or(uint64_t(1) << bit);
   return s;
 }
 
